@@ -1,0 +1,99 @@
+"""Named synthetic workloads shaped like the thesis's ED benchmarks.
+
+The thesis's clusters exist only in its (missing) figures, so each workload is
+a concrete periodic cluster chosen here; its periodicity vectors are stated in
+the docstring of each function.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from .lattice import (Cluster, build_problem, chain_lattice, kagome_lattice, square_lattice,
+                      triangular_lattice)
+
+PI = math.pi
+
+
+def chain(N: int, J1: float = 1.0, J2: float = 0.0, *, translations=False, reflection=False,
+          k: int = 0, irrep: str = "A1", spinflip=None, n_up=None, n_sublat=None, max_table_bytes=96 * 1024):
+    """Periodic chain of N sites; momentum 2*pi*k/N."""
+    cl = Cluster(chain_lattice(), [[N, 0], [0, 1]])
+    J = {1: J1}
+    if J2:
+        J[2] = J2
+    point = "full" if reflection else "none"
+    if not reflection and irrep == "A1":
+        irrep = "A"
+    return build_problem(f"chain{N}", cl, J=J, n_up=n_up, point=point, translations=translations,
+                         k=(2 * PI * k / N, 0.0), irrep=irrep, spinflip=spinflip, n_sublat=n_sublat,
+                         max_table_bytes=max_table_bytes)
+
+
+def square(P, J1=1.0, J2=0.0, *, k=(0.0, 0.0), irrep="A1", point="full", spinflip=None, n_up=None,
+           n_sublat=None, max_table_bytes=96 * 1024, translations=True):
+    cl = Cluster(square_lattice(), P)
+    J = {1: J1}
+    if J2:
+        J[2] = J2
+    return build_problem(f"square{cl.N}", cl, J=J, n_up=n_up, point=point, k=k, irrep=irrep,
+                         spinflip=spinflip, n_sublat=n_sublat, max_table_bytes=max_table_bytes,
+                         translations=translations)
+
+
+def triangular(P, J1=1.0, J2=0.0, *, k=(0.0, 0.0), irrep="A1", point="full", spinflip=None, n_up=None,
+               n_sublat=None, max_table_bytes=96 * 1024, translations=True):
+    cl = Cluster(triangular_lattice(), P)
+    J = {1: J1}
+    if J2:
+        J[2] = J2
+    return build_problem(f"triangular{cl.N}", cl, J=J, n_up=n_up, point=point, k=k, irrep=irrep,
+                         spinflip=spinflip, n_sublat=n_sublat, max_table_bytes=max_table_bytes,
+                         translations=translations)
+
+
+def kagome(P, J1=1.0, J2=0.0, Jchi=0.0, *, k=(0.0, 0.0), irrep="A", point="rot", spinflip=None,
+           n_up=None, n_sublat=None, max_table_bytes=96 * 1024, translations=True):
+    """Kagome cluster; the scalar chirality breaks mirrors, so the default point group is C6."""
+    cl = Cluster(kagome_lattice(), P)
+    J = {1: J1}
+    if J2:
+        J[2] = J2
+    return build_problem(f"kagome{cl.N}", cl, J=J, Jchi=Jchi, n_up=n_up, point=point, k=k, irrep=irrep,
+                         spinflip=spinflip, n_sublat=n_sublat, max_table_bytes=max_table_bytes,
+                         translations=translations)
+
+
+# ---------------------------------------------------------------------------
+# the five workloads
+# ---------------------------------------------------------------------------
+def chain16():
+    """Heisenberg chain N=16, periodic, J1=1, Sz=0, no spatial symmetry (dim 12870)."""
+    return chain(16, 1.0)
+
+
+def square32(irrep="A1", momentum="Gamma"):
+    """32-site tilted square cluster a1=(4,4), a2=(4,-4); J1=1, J2=0.5; T32 x C4v, Sz=0."""
+    k = (0.0, 0.0) if momentum == "Gamma" else (PI, PI)
+    return square([[4, 4], [4, -4]], 1.0, 0.5, k=k, irrep=irrep)
+
+
+def kagome36(spinflip=1, irrep="A"):
+    """36-site kagome, Bravais a1=2A1+2A2, a2=-2A1+4A2 (12 cells); J1=1, J2=0.2, Jchi=0.3
+    on every triangle; T12 x C6 x Z2 (144 elements), Gamma sector, Sz=0."""
+    return kagome([[2, 2], [-2, 4]], 1.0, 0.2, 0.3, irrep=irrep, spinflip=spinflip)
+
+
+def triangular24(k=(0.0, 0.0), irrep="A1"):
+    """24-site triangular torus a1=(5,1), a2=(4,-4) in lattice coordinates; J1=1, J2=0.125.
+
+    No 24-site triangular torus has a sixfold axis (24 is not a^2+ab+b^2); this
+    one keeps the largest point group available at N=24, C2v, so T24 x C2v = 96.
+    """
+    return triangular([[5, 1], [4, -4]], 1.0, 0.125, k=k, irrep=irrep)
+
+
+def square40(spinflip=1, irrep="A"):
+    """40-site square cluster a1=(6,2), a2=(-2,6); J1=1, J2=0.55; T40 x C4 x Z2 (320)."""
+    return square([[6, 2], [-2, 6]], 1.0, 0.55, irrep=irrep, point="full", spinflip=spinflip)

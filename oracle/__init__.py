@@ -1,0 +1,11 @@
+"""CPU FP64 oracle for the symmetry-adapted H.x path -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline arm may
+import this package.  It shares no code with the CUDA library
+(paper_2210_03511_gb300); the two meet only through the seeded inputs of
+`edinputs`.  Every function is pinned by tests/test_oracle_*.py against
+closed forms, the thesis's worked examples, invariants and brute force.
+"""
+from .core import (apply, basis, binom, build, csr, dense_sz, lowest_eigs, num_threads, projector_matrix,  # noqa: F401
+                   rep, rows, sector_dim_formula, sz_states)
+from .ops import bond_matrix, chirality_matrix  # noqa: F401
