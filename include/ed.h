@@ -1,0 +1,225 @@
+/*
+ * ed.h -- C ABI of libed, a single-GPU (sm_103a) library for the matrix-free
+ * Hamiltonian application y = H.x of spin-1/2 Heisenberg-type models in a
+ * symmetry-adapted, fixed-Sz basis, and for Lanczos eigensolves built on it.
+ *
+ * The problem statement follows A. Wietek's thesis, chapter "Symmetries and
+ * Parallelization for Large-Scale Exact Diagonalization":
+ *   H = sum_b J_b S_i.S_j  (Eq. heisenbergallover)
+ *     + sum_t Jchi_t S_i.(S_j x S_k)  (Eq. scalarchirality, Eq. chiralhamiltonian),
+ *   a site-permutation group G with an optional spin flip (Eq. spinflipsymmetry,
+ *   Eq. tensorchar) and a one-dimensional irrep chi of G
+ *   (Eq. symmetryadaptedwavefunction1d), and a sector of fixed S^z_tot
+ *   (Eq. sztotal).
+ *
+ * Conventions
+ *   - A spin configuration is the integer sum_k sigma_k 2^(N-k), site 1 most
+ *     significant, spin up = 1 (Eq. numberforspinconfig).  With 0-based sites,
+ *     site s is bit N-1-s.
+ *   - Group elements act actively: the spin on site i moves to site perm[g][i];
+ *     a spin-flip element also complements every spin.
+ *   - Sites are numbered so that sublattice X is the contiguous block
+ *     [X*m, (X+1)*m), m = n_sites/n_sublat, with sublattice 0 in the most
+ *     significant bits (sublattice-coding section, "Generic sublattice coding
+ *     algorithm").  Every group element must map each block onto one block
+ *     (sublattice stability).
+ *   - The basis of a sector is the ascending list of orbit representatives
+ *     (smallest integer in the orbit, Eq. representativecondition) whose
+ *     projector sum_g conj(chi(g)) g|sigma> is non-zero; the index of a state is
+ *     its position in that list.  The symmetric state of representative sigma
+ *     has norm^2 = |G| |Stab(sigma)|.
+ *   - Matrix elements between representatives (Eq. matrixelementrepresentatives
+ *     with the projector of Eq. symmetryadaptedwavefunction1d_lsed):
+ *       <tau~|H_k|sigma~> = conj(chi(g_tau)) sqrt(|Stab tau~|/|Stab sigma~|) <tau|H_k|sigma~>.
+ *
+ * Errors: every call returns an ed_status; ed_last_error() gives a message for
+ * the calling thread.  No call throws.  Device pointers are CUDA device
+ * pointers on the current device; host pointers are read only during the call.
+ */
+#ifndef ED_H
+#define ED_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ED_OK = 0,
+    ED_ERR_ARG = 1,                     /* a null pointer, a size out of range, an unsupported dtype */
+    ED_ERR_NOT_GROUP = 2,               /* perm/spinflip not closed under composition, or element 0 not the identity */
+    ED_ERR_NOT_SYMMETRIC = 3,           /* some element does not map the bond or triangle set onto itself */
+    ED_ERR_NOT_SUBLATTICE_STABLE = 4,   /* some element splits a sublattice block */
+    ED_ERR_CHAR_NOT_HOMOMORPHISM = 5,   /* chi(gh) != chi(g)chi(h), |chi| != 1, or chi(identity) != 1 */
+    ED_ERR_SPINFLIP_SZ = 6,             /* a spin-flip element with 2*n_up != n_sites */
+    ED_ERR_EMPTY_SECTOR = 7,            /* the sector has dimension 0 */
+    ED_ERR_NOMEM = 8,                   /* the allocator returned NULL */
+    ED_ERR_INDEX_NOT_FOUND = 9,         /* a compatible representative was missing from the basis (internal error) */
+    ED_ERR_TIMEOUT = 10,                /* a bounded device wait ran out */
+    ED_ERR_NOT_CONVERGED = 11,          /* Lanczos reached max_iter before the tolerance */
+    ED_ERR_CUDA = 12,                   /* a CUDA runtime call failed; the message holds its text */
+    ED_ERR_TABLE_TOO_LARGE = 13         /* the sublattice tables do not fit the device's shared memory */
+} ed_status;
+
+/* Element type of vectors passed to ed_apply / ed_lanczos.
+ * ED_F64/ED_F32 need a real Hamiltonian and real characters;
+ * ED_C128/ED_C64 are interleaved (re, im) pairs. */
+typedef enum { ED_F64 = 0, ED_F32 = 1, ED_C64 = 2, ED_C128 = 3 } ed_dtype;
+
+/* A CUDA stream (cudaStream_t); NULL is the legacy default stream. */
+typedef struct CUstream_st* ed_stream;
+
+/* Device-memory provider.  alloc returns device memory of at least `bytes`
+ * bytes usable on `stream`, or NULL; free releases it.  When the allocator
+ * pointer passed to a call is NULL the library uses cudaMalloc/cudaFree. */
+typedef struct {
+    void* (*alloc)(size_t bytes, ed_stream stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, ed_stream stream, void* ctx);
+    void* ctx;
+} ed_allocator;
+
+/* One symmetry sector.  All pointers are HOST pointers read during the call. */
+typedef struct {
+    int32_t n_sites;          /* N, 2 <= N <= 64 */
+    int32_t n_up;             /* number of up spins, S^z = n_up - N/2 */
+    int32_t n_sym;            /* |G| >= 1; element 0 must be the identity without flip */
+    const int32_t* perm;      /* [n_sym][n_sites], row-major: spin on site i moves to perm[g][i] */
+    const uint8_t* spinflip;  /* [n_sym] 0/1, or NULL for no flips */
+    const double* chi;        /* [n_sym][2] = (Re, Im) of chi(g), |chi(g)| = 1 */
+    int32_t n_sublat;         /* number of sublattice blocks, divides n_sites */
+} ed_sector;
+
+/* The Hamiltonian.  Host pointers, read during the call. */
+typedef struct {
+    int32_t n_bonds;
+    const int32_t* bond;      /* [n_bonds][2] site pairs, i != j */
+    const double* J;          /* [n_bonds] couplings of S_i.S_j */
+    int32_t n_tri;
+    const int32_t* tri;       /* [n_tri][3] sites (i, j, k) of S_i.(S_j x S_k), distinct */
+    const double* Jchi;       /* [n_tri] couplings */
+} ed_terms;
+
+typedef struct ed_basis ed_basis;              /* opaque; owns device memory */
+typedef struct ed_hamiltonian ed_hamiltonian;  /* opaque; basis + prepared terms */
+
+/* ed_basis_build -- enumerate the sector's basis on the device.
+ *
+ * Validates the sector (group closure, identity first, chi a homomorphism,
+ * spin flips only at S^z = 0, sublattice stability), prepares the
+ * sublattice-coding lookup tables Rep_X, Sym_X and SymmetryAction_X
+ * (Alg. "Preparation of lookup tables for sublattice coding algorithm",
+ * Eqs. sublatsymdef, sublatrepdef, repsymdef, symactiondef), enumerates every
+ * popcount-n_up state in increasing order, keeps those that are their own
+ * representative (Alg. "Sublattice coding algorithm for finding the
+ * representative") with a non-zero projector, and builds the prefix table
+ * Limits (Alg. "Preparation of the distributed and symmetrized Hilbert space",
+ * on one device and without the hash distribution).
+ * Device memory comes from `alloc` (or cudaMalloc when NULL) and is owned by
+ * the basis until ed_basis_free.  Runs on `stream` and synchronises it.
+ * Returns ED_ERR_EMPTY_SECTOR (and no basis) for a zero-dimensional sector. */
+ed_status ed_basis_build(const ed_sector* sector, const ed_allocator* alloc, ed_stream stream, ed_basis** out);
+
+/* Dimension D of the sector. */
+ed_status ed_basis_dim(const ed_basis* basis, int64_t* dim);
+
+/* Copy the basis to HOST arrays: reps[D] as uint64 (ascending), stab[D] = |Stab(rep)|.
+ * Either pointer may be NULL. */
+ed_status ed_basis_export(const ed_basis* basis, uint64_t* reps, uint16_t* stab);
+
+/* ed_sector_tables -- validate a sector and return its sublattice-coding
+ * tables without touching the device (host only; for inspection and tests).
+ * Performs the same checks as ed_basis_build and returns the same errors.
+ * With m = n_sites/n_sublat and S = 2^m:
+ *   rep[X*S + s] = Rep_X(s) (0xFFFF if no element maps block X onto block 0);
+ *   sym_ids[sym_off[X*(S+1) + s] .. sym_off[X*(S+1) + s + 1]) = Sym_X(s);
+ *   sa[(g*n_sublat + X)*S + s] = SymmetryAction_X(g, s), an m-bit substate of
+ *   block dest[g*n_sublat + X].
+ * Any output pointer may be NULL (call once with NULLs to learn *n_sym_ids).
+ * Sizes: rep n_sublat*S, sym_off n_sublat*(S+1), sa n_sym*n_sublat*S,
+ * dest n_sym*n_sublat, sym_ids *n_sym_ids. */
+ed_status ed_sector_tables(const ed_sector* sector, uint16_t* rep, uint32_t* sym_off, uint16_t* sym_ids,
+                           int64_t* n_sym_ids, uint16_t* sa, uint8_t* dest);
+
+void ed_basis_free(ed_basis* basis);
+
+/* ed_hamiltonian_create -- bind terms to a basis.
+ * Checks that every group element maps the bond set (with couplings) and the
+ * triangle set (with orientation and coupling) onto itself, splits each
+ * S_i.S_j into its Ising part and the exchange 1/2(S+_i S-_j + S-_i S+_j)
+ * (non-branching terms, Eq. nonbranchingcondition) and each chirality term
+ * into spin-pair flips weighted by the third spin, and uploads the flip list.
+ * The basis must outlive the Hamiltonian.  Complex terms (any Jchi != 0) or
+ * complex characters need ED_C64/ED_C128 vectors. */
+ed_status ed_hamiltonian_create(const ed_basis* basis, const ed_terms* terms, ed_hamiltonian** out);
+
+/* 1 if the Hamiltonian in this sector is real symmetric (real vectors allowed). */
+ed_status ed_hamiltonian_is_real(const ed_hamiltonian* h, int32_t* is_real);
+
+void ed_hamiltonian_free(ed_hamiltonian* h);
+
+/* ed_apply -- y = H x for nvec vectors (1 <= nvec <= 8).
+ *
+ * x and y are DEVICE arrays of `dtype`, column-major [nvec][D] (vector v
+ * starts at element v*D), owned by the caller; y is overwritten; x and y must
+ * not overlap.  Matrix-free (section "Distributed and hybrid memory
+ * parallelization", Eqs. branchingsum, outputvector): each row sigma_i of y is
+ * produced by one owner from the non-branching terms applied to sigma_i, the
+ * representative and g_tau of each image by sublattice coding, and the index
+ * of the representative by Limits + binary search (Alg. "Parallel
+ * matrix-vector multiply for a non-branching term", restated in pull form:
+ * y_i = sum_j conj(H_ji) x_j, valid because H is Hermitian).
+ * Asynchronous on `stream`. */
+ed_status ed_apply(const ed_hamiltonian* h, ed_dtype dtype, const void* x, void* y, int32_t nvec, ed_stream stream);
+
+/* Counters of the most recent ed_apply on this Hamiltonian (synchronises stream):
+ * number of off-diagonal terms whose representative was found (gathers per
+ * vector) and number of images skipped as incompatible. */
+ed_status ed_apply_counters(const ed_hamiltonian* h, ed_stream stream, int64_t* gathers, int64_t* skipped);
+
+typedef struct {
+    ed_dtype dtype;        /* vector type: F64/C128 plain, F32/C64 mixed (FP64 reductions) */
+    int32_t n_eig;         /* lowest eigenvalues wanted, 1..8 */
+    double tol;            /* convergence tolerance on eigenvalues (relative, e.g. 1e-10) */
+    int32_t max_iter;      /* Lanczos steps at most (<= 2000) */
+    int32_t reorth;        /* 1 = full reorthogonalisation (classical Gram-Schmidt twice) against stored vectors */
+    uint64_t seed;         /* start vector v1(state) = keyed SplitMix64 uniform in [-1,1), normalised */
+    int32_t refine;        /* mixed precision: FP64 H.x applications for the Rayleigh quotient of the Ritz vectors */
+    int32_t check_every;   /* T-matrix eigensolve every this many steps (>= 1) */
+} ed_lanczos_opts;
+
+typedef struct {
+    int32_t iters;             /* Lanczos steps taken */
+    int32_t converged;         /* 1 if all n_eig reached tol */
+    int32_t n_apply;           /* H.x applications (including refinement) */
+    double ritz[8];            /* T-matrix eigenvalues at exit (in the vector dtype's precision) */
+    double resid_bound[8];     /* beta_n |s_n,k|: Lanczos residual bound of each Ritz pair */
+    double refined[8];         /* FP64 Rayleigh quotients of the Ritz vectors (when refine) */
+    double refined_resid[8];   /* FP64 ||H v - E v|| of the normalised Ritz vectors (when refine) */
+    double seconds;            /* wall time of the call */
+} ed_lanczos_report;
+
+/* ed_lanczos -- lowest eigenvalues of H by the Lanczos recursion
+ * (Eqs. lanczosrecursionabbrev, tmatrix; Algs. "Real-symmetric Lanczos step"
+ * and "Complex-Hermitian Lanczos step") with FP64 inner products,
+ * optional full reorthogonalisation, and the tridiagonal eigenproblem solved in
+ * FP64 every check_every steps.  evals: HOST [n_eig] (refined values when
+ * opts.refine, else Ritz values).  evecs: DEVICE [n_eig][D] of the vector dtype,
+ * or NULL (needs reorth = 1 to be filled).  Workspace comes from cudaMalloc
+ * and is released before return.  Synchronous.  Returns
+ * ED_ERR_NOT_CONVERGED if max_iter is reached first (results still written). */
+ed_status ed_lanczos(const ed_hamiltonian* h, const ed_lanczos_opts* opts, double* evals, void* evecs,
+                     ed_lanczos_report* report, ed_stream stream);
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* ed_last_error(void);
+
+/* Library version string. */
+const char* ed_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ED_H */

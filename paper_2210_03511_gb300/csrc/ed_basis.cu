@@ -1,0 +1,450 @@
+// Device basis construction (Alg. "Preparation of the distributed and
+// symmetrized Hilbert space" on one GPU, with the representative test of
+// Alg. "Sublattice coding algorithm for finding the representative").
+//
+// The candidate space is cut into segments by the value v of the most
+// significant sublattice block: a representative's top block equals MinRep,
+// so only values with Rep_0(v) = v can start a representative.  Inside a
+// segment the remaining L = N - m bits run over all integers with popcount
+// n_up - popcount(v) in increasing order, so the concatenation of segments in
+// order of v is sorted.  Each thread owns a chunk of CH consecutive
+// candidates: it unranks the first one (combinatorial number system) and
+// steps with the next-same-popcount rule.  A first pass counts kept states per
+// chunk, an exclusive scan gives output offsets, a second pass writes them.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ed_device.cuh"
+#include "ed_internal.h"
+
+namespace ed {
+
+__constant__ uint64_t c_binom[65][65];
+
+static const int CH = 128;  // candidates per thread
+
+struct Seg {
+    uint32_t v;         // top-block value
+    int32_t k;          // ones in the remaining L bits
+    uint64_t size;      // C(L, k)
+    uint64_t chunk0;    // first chunk index
+};
+
+template <typename W>
+__device__ __forceinline__ W unrank(uint64_t r, int L, int k) {
+    W v = 0;
+    for (int b = L - 1; b >= 0 && k > 0; --b) {
+        const uint64_t c = c_binom[b][k];
+        if (r >= c) {
+            v |= (W)1 << b;
+            r -= c;
+            --k;
+        }
+    }
+    return v;
+}
+
+template <typename W>
+__device__ __forceinline__ W next_same_popcount(W v) {
+    const W c = v & (~v + 1);
+    const W r = v + c;
+    const int tz = (sizeof(W) == 8) ? (__ffsll((long long)c) - 1) : (__ffs((int)c) - 1);
+    return (((r ^ v) >> 2) >> tz) | r;
+}
+
+struct EnumArgs {
+    DevTables dt;
+    const Seg* segs;
+    int n_segs;
+    uint64_t n_chunks;
+    int L;
+    uint32_t* counts;          // pass 0 output
+    const uint64_t* offsets;   // pass 1 input
+    void* reps;                // pass 1 output (W)
+    uint16_t* stab;            // pass 1 output
+};
+
+template <typename W, typename SAT, int PASS>
+__global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    stage_blob(smem, a.dt.blob, a.dt.blob_bytes);
+    __syncthreads();
+    const TabView<SAT> t = tab_view<SAT>(smem, a.dt);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n_chunks; c += stride) {
+        // segment of chunk c
+        int lo = 0, hi = a.n_segs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.segs[mid].chunk0 <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        const Seg sg = a.segs[lo];
+        const uint64_t r0 = (c - sg.chunk0) * CH;
+        const uint64_t n = min((uint64_t)CH, sg.size - r0);
+        W suf = unrank<W>(r0, a.L, sg.k);
+        const W top = (W)sg.v << a.L;
+        uint32_t kept = 0;
+        uint64_t out = PASS ? a.offsets[c] : 0;
+        for (uint64_t i = 0; i < n; ++i) {
+            const W s = top | suf;
+            int ns;
+            bool cp;
+            if (is_rep<W, SAT>(s, t, ns, cp) && cp) {
+                if (PASS) {
+                    ((W*)a.reps)[out] = s;
+                    a.stab[out] = (uint16_t)ns;
+                    ++out;
+                }
+                ++kept;
+            }
+            if (sg.k > 0 && i + 1 < n) suf = next_same_popcount<W>(suf);
+        }
+        if (!PASS) a.counts[c] = kept;
+    }
+}
+
+// ---------------------------------------------------------------- scan (u32 counts -> u64 exclusive offsets)
+static const int SCAN_TILE = 4096;
+
+__global__ void scan_tile_sums(const uint32_t* in, uint64_t n, uint64_t* tile_sums) {
+    __shared__ uint64_t red[32];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    uint64_t acc = 0;
+    for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
+        if (base + i < n) acc += in[base + i];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        acc = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0;
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (threadIdx.x == 0) tile_sums[blockIdx.x] = acc;
+    }
+}
+
+// single block: exclusive scan of tile sums in place, total in *total
+__global__ void scan_tiles_serial(uint64_t* tile_sums, uint64_t n_tiles, uint64_t* total) {
+    __shared__ uint64_t carry;
+    __shared__ uint64_t warp_tot[32];
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint64_t base = 0; base < n_tiles; base += blockDim.x) {
+        const uint64_t i = base + threadIdx.x;
+        uint64_t v = i < n_tiles ? tile_sums[i] : 0;
+        // inclusive warp scan
+        uint64_t x = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint64_t y = __shfl_up_sync(0xffffffffu, x, o);
+            if ((threadIdx.x & 31) >= o) x += y;
+        }
+        if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            uint64_t w = threadIdx.x < (blockDim.x >> 5) ? warp_tot[threadIdx.x] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                uint64_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (threadIdx.x >= o) w += y;
+            }
+            warp_tot[threadIdx.x] = w;  // inclusive over warps
+        }
+        __syncthreads();
+        const int wi = threadIdx.x >> 5;
+        const uint64_t warp_off = wi ? warp_tot[wi - 1] : 0;
+        if (i < n_tiles) tile_sums[i] = carry + warp_off + x - v;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void scan_tile_apply(const uint32_t* in, uint64_t n, const uint64_t* tile_off, uint64_t* out) {
+    // one block per tile, sequential inside each thread's contiguous piece
+    __shared__ uint64_t part[1024];
+    const uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
+    const int per = SCAN_TILE / blockDim.x;
+    uint64_t acc = 0;
+    const uint64_t my0 = base + (uint64_t)threadIdx.x * per;
+    for (int i = 0; i < per; ++i)
+        if (my0 + i < n) acc += in[my0 + i];
+    part[threadIdx.x] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint64_t run = tile_off[blockIdx.x];
+        for (unsigned j = 0; j < blockDim.x; ++j) {
+            const uint64_t t = part[j];
+            part[j] = run;
+            run += t;
+        }
+    }
+    __syncthreads();
+    uint64_t run = part[threadIdx.x];
+    for (int i = 0; i < per; ++i)
+        if (my0 + i < n) {
+            out[my0 + i] = run;
+            run += in[my0 + i];
+        }
+}
+
+// ---------------------------------------------------------------- Limits
+// Two-level Limits: for top-block value v, bucket b = next q_v bits;
+// key = base_v + b; limits[key] = first index with state >= (v, b).
+template <typename W>
+__global__ void limits_kernel(const W* reps, uint64_t D, const uint32_t* seg_base, const uint8_t* seg_q,
+                              const uint64_t* v_lo, int S, int L, uint32_t* limits, uint64_t n_keys) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t key = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; key < n_keys; key += stride) {
+        // find v with seg_base[v] <= key < seg_base[v+1]
+        int lo = 0, hi = S - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (seg_base[mid] <= key) lo = mid;
+            else hi = mid - 1;
+        }
+        const int v = lo;
+        const uint64_t b = key - seg_base[v];
+        const int q = seg_q[v];
+        const W target = ((W)v << L) | (W)(q ? (b << (L - q)) : 0);
+        // lower_bound inside v's range
+        uint64_t a0 = v_lo[v], a1 = v_lo[v + 1];
+        while (a0 < a1) {
+            const uint64_t mid = (a0 + a1) >> 1;
+            if (reps[mid] < target) a0 = mid + 1;
+            else a1 = mid;
+        }
+        limits[key] = (uint32_t)a0;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) limits[n_keys] = (uint32_t)D;
+}
+
+// ---------------------------------------------------------------- host
+ed_status upload_tables(ed_basis* b, cudaStream_t s) {
+    const HostTables& t = b->ht;
+    const int S = 1 << t.m;
+    const int sab = t.m <= 8 ? 1 : 2;
+    size_t off = 0;
+    auto al = [&](size_t n) {
+        off = (off + 15) & ~(size_t)15;
+        size_t o = off;
+        off += n;
+        return (uint32_t)o;
+    };
+    DevTables& d = b->dt;
+    d.N = t.N; d.G = t.G; d.n_sub = t.n_sub; d.m = t.m; d.sa_bytes = sab;
+    d.off_rep = al((size_t)t.n_sub * S * 2);
+    d.off_symoff = al((size_t)t.n_sub * (S + 1) * 4);
+    d.off_symids = al(std::max<size_t>(t.sym_ids.size(), 1) * 2);
+    d.off_sa = al((size_t)t.G * t.n_sub * S * sab);
+    d.off_src = al((size_t)t.G * t.n_sub);
+    d.off_chi = al((size_t)t.G * 16);
+    d.off_chione = al((size_t)t.G);
+    d.off_sqrt = al((size_t)2 * (t.G + 1) * 8);
+    d.off_chif = al((size_t)t.G * 8);
+    d.off_sqrtf = al((size_t)2 * (t.G + 1) * 4);
+    const size_t total = (off + 15) & ~(size_t)15;
+    d.blob_bytes = total;
+    std::vector<uint8_t> h(total, 0);
+    memcpy(&h[d.off_rep], t.rep.data(), t.rep.size() * 2);
+    memcpy(&h[d.off_symoff], t.sym_off.data(), t.sym_off.size() * 4);
+    if (!t.sym_ids.empty()) memcpy(&h[d.off_symids], t.sym_ids.data(), t.sym_ids.size() * 2);
+    if (sab == 1) {
+        for (size_t i = 0; i < t.sa.size(); ++i) h[d.off_sa + i] = (uint8_t)t.sa[i];
+    } else {
+        memcpy(&h[d.off_sa], t.sa.data(), t.sa.size() * 2);
+    }
+    memcpy(&h[d.off_src], t.src.data(), t.src.size());
+    memcpy(&h[d.off_chi], t.chi.data(), (size_t)t.G * 16);
+    memcpy(&h[d.off_chione], t.chi_one.data(), (size_t)t.G);
+    std::vector<double> sq(2 * (size_t)(t.G + 1));
+    for (int k = 0; k <= t.G; ++k) {
+        sq[k] = sqrt((double)k);
+        sq[t.G + 1 + k] = k ? 1.0 / sqrt((double)k) : 0.0;
+    }
+    memcpy(&h[d.off_sqrt], sq.data(), sq.size() * 8);
+    std::vector<float> chif(2 * (size_t)t.G), sqf(sq.size());
+    for (size_t i = 0; i < chif.size(); ++i) chif[i] = (float)t.chi[i];
+    for (size_t i = 0; i < sq.size(); ++i) sqf[i] = (float)sq[i];
+    memcpy(&h[d.off_chif], chif.data(), chif.size() * 4);
+    memcpy(&h[d.off_sqrtf], sqf.data(), sqf.size() * 4);
+    b->tables.bytes = total;
+    b->tables.p = b->alloc.get(total, s);
+    if (!b->tables.p) return fail(ED_ERR_NOMEM, "table allocation failed");
+    ED_CUDA(cudaMemcpyAsync(b->tables.p, h.data(), total, cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    d.blob = (const uint8_t*)b->tables.p;
+    return ED_OK;
+}
+
+template <typename W, typename SAT, int PASS>
+static ed_status launch_enum(const EnumArgs& a, size_t smem, int sms, cudaStream_t s) {
+    auto k = enum_kernel<W, SAT, PASS>;
+    ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
+    if (per_sm < 1) return fail(ED_ERR_TABLE_TOO_LARGE, "lookup tables (%zu bytes) do not fit shared memory", smem);
+    uint64_t want = (a.n_chunks + 255) / 256;
+    uint64_t grid = std::min<uint64_t>(want, (uint64_t)sms * per_sm * 4);
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, 256, smem, s>>>(a);
+    ED_CUDA(cudaGetLastError());
+    return ED_OK;
+}
+
+template <typename W, typename SAT>
+static ed_status enum_both(ed_basis* b, EnumArgs& a, size_t smem, int sms, cudaStream_t s, int pass) {
+    return pass == 0 ? launch_enum<W, SAT, 0>(a, smem, sms, s) : launch_enum<W, SAT, 1>(a, smem, sms, s);
+}
+
+static ed_status run_enum(ed_basis* b, EnumArgs& a, int pass, int sms, cudaStream_t s) {
+    const size_t smem = b->dt.blob_bytes;
+    const bool w8 = b->word == 8, s8 = b->dt.sa_bytes == 1;
+    if (w8) return s8 ? enum_both<uint64_t, uint8_t>(b, a, smem, sms, s, pass)
+                      : enum_both<uint64_t, uint16_t>(b, a, smem, sms, s, pass);
+    return s8 ? enum_both<uint32_t, uint8_t>(b, a, smem, sms, s, pass)
+              : enum_both<uint32_t, uint16_t>(b, a, smem, sms, s, pass);
+}
+
+namespace {
+struct Scratch {
+    const Alloc* A;
+    cudaStream_t s;
+    std::vector<std::pair<void*, size_t>> bufs;
+    void* get(size_t n) {
+        void* p = A->get(n, s);
+        if (p) bufs.push_back({p, n});
+        return p;
+    }
+    ~Scratch() {
+        cudaStreamSynchronize(s);
+        for (auto& b : bufs) A->put(b.first, b.second, s);
+    }
+};
+}  // namespace
+
+ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
+    const HostTables& t = b->ht;
+    ED_CUDA(cudaGetDevice(&b->device));
+    int sms = 0;
+    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+    b->word = t.N <= 32 ? 4 : 8;
+    // binomials
+    {
+        std::vector<uint64_t> C(65 * 65, 0);
+        for (int n = 0; n <= 64; ++n) {
+            C[n * 65 + 0] = 1;
+            for (int k = 1; k <= n; ++k) C[n * 65 + k] = C[(n - 1) * 65 + k - 1] + (k <= n - 1 ? C[(n - 1) * 65 + k] : 0);
+        }
+        ED_CUDA(cudaMemcpyToSymbol(c_binom, C.data(), C.size() * 8));
+    }
+    ed_status st = upload_tables(b, s);
+    if (st != ED_OK) return st;
+    const int m = t.m, L = t.N - m, S = 1 << m;
+    std::vector<Seg> segs;
+    uint64_t chunks = 0;
+    for (int v = 0; v < S; ++v) {
+        if (t.rep[v] != v) continue;  // block 0: Rep_0(v) = v is necessary
+        const int k = t.n_up - __builtin_popcount((unsigned)v);
+        if (k < 0 || k > L) continue;
+        uint64_t C = 1;
+        for (int i = 0; i < k; ++i) C = C * (uint64_t)(L - i) / (uint64_t)(i + 1);
+        Seg sg{(uint32_t)v, k, C, chunks};
+        segs.push_back(sg);
+        chunks += (C + CH - 1) / CH;
+    }
+    if (segs.empty() || chunks == 0) return fail(ED_ERR_EMPTY_SECTOR, "sector has dimension 0");
+    Scratch sc{&b->alloc, s, {}};
+    Seg* d_segs = (Seg*)sc.get(segs.size() * sizeof(Seg));
+    uint32_t* d_counts = (uint32_t*)sc.get(chunks * 4);
+    uint64_t* d_offs = (uint64_t*)sc.get(chunks * 8);
+    const uint64_t n_tiles = (chunks + SCAN_TILE - 1) / SCAN_TILE;
+    uint64_t* d_tiles = (uint64_t*)sc.get(n_tiles * 8 + 8);
+    uint64_t* d_total = (uint64_t*)sc.get(8);
+    if (!d_segs || !d_counts || !d_offs || !d_tiles || !d_total) return fail(ED_ERR_NOMEM, "enumeration scratch");
+    ED_CUDA(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, s));
+    EnumArgs a{};
+    a.dt = b->dt;
+    a.segs = d_segs;
+    a.n_segs = (int)segs.size();
+    a.n_chunks = chunks;
+    a.L = L;
+    a.counts = d_counts;
+    st = run_enum(b, a, 0, sms, s);
+    if (st != ED_OK) return st;
+    scan_tile_sums<<<(unsigned)n_tiles, 256, 0, s>>>(d_counts, chunks, d_tiles);
+    scan_tiles_serial<<<1, 1024, 0, s>>>(d_tiles, n_tiles, d_total);
+    scan_tile_apply<<<(unsigned)n_tiles, 256, 0, s>>>(d_counts, chunks, d_tiles, d_offs);
+    ED_CUDA(cudaGetLastError());
+    uint64_t D = 0;
+    ED_CUDA(cudaMemcpyAsync(&D, d_total, 8, cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    if (D == 0) return fail(ED_ERR_EMPTY_SECTOR, "sector has dimension 0");
+    if (D >= 0xFFFFFFFFull) return fail(ED_ERR_ARG, "dimension %llu exceeds 2^32-1", (unsigned long long)D);
+    b->dim = (int64_t)D;
+    b->reps.bytes = D * b->word;
+    b->reps.p = b->alloc.get(b->reps.bytes, s);
+    b->stab.bytes = D * 2;
+    b->stab.p = b->alloc.get(b->stab.bytes, s);
+    if (!b->reps.p || !b->stab.p) return fail(ED_ERR_NOMEM, "basis allocation (%llu states)", (unsigned long long)D);
+    a.offsets = d_offs;
+    a.reps = b->reps.p;
+    a.stab = (uint16_t*)b->stab.p;
+    st = run_enum(b, a, 1, sms, s);
+    if (st != ED_OK) return st;
+    // per-segment dimensions from the chunk offsets
+    std::vector<uint64_t> offs(chunks);
+    ED_CUDA(cudaMemcpyAsync(offs.data(), d_offs, chunks * 8, cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    std::vector<uint64_t> v_lo(S + 1, 0);
+    {
+        // v_lo[v] = first index with top block >= v
+        std::vector<uint64_t> start(S, UINT64_MAX);
+        for (size_t i = 0; i < segs.size(); ++i) start[segs[i].v] = offs[segs[i].chunk0];
+        uint64_t next = D;
+        v_lo[S] = D;
+        for (int v = S - 1; v >= 0; --v) {
+            if (start[v] != UINT64_MAX) next = start[v];
+            v_lo[v] = next;
+        }
+    }
+    // two-level Limits: q_v bits for top value v so buckets hold ~16 states
+    std::vector<uint32_t> seg_base(S + 1, 0);
+    std::vector<uint8_t> seg_q(S, 0);
+    uint64_t keys = 0;
+    for (int v = 0; v < S; ++v) {
+        const uint64_t Dv = v_lo[v + 1] - v_lo[v];
+        int q = 0;
+        while (q < L && (Dv >> q) > 16) ++q;
+        seg_q[v] = (uint8_t)q;
+        seg_base[v] = (uint32_t)keys;
+        keys += (uint64_t)1 << q;
+    }
+    seg_base[S] = (uint32_t)keys;
+    b->prefix_bits = L;
+    // device image of the Limits directory: [S+1] base, [S] q (padded), then limits
+    b->limits.bytes = (S + 1) * 4 + ((S + 15) & ~15) + (keys + 1) * 4;
+    b->limits.p = b->alloc.get(b->limits.bytes, s);
+    if (!b->limits.p) return fail(ED_ERR_NOMEM, "limits allocation");
+    uint8_t* base = (uint8_t*)b->limits.p;
+    ED_CUDA(cudaMemcpyAsync(base, seg_base.data(), (S + 1) * 4, cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(base + (S + 1) * 4, seg_q.data(), S, cudaMemcpyHostToDevice, s));
+    uint64_t* d_vlo = (uint64_t*)sc.get((S + 1) * 8);
+    if (!d_vlo) return fail(ED_ERR_NOMEM, "limits scratch");
+    ED_CUDA(cudaMemcpyAsync(d_vlo, v_lo.data(), (S + 1) * 8, cudaMemcpyHostToDevice, s));
+    uint32_t* d_lim = (uint32_t*)(base + (S + 1) * 4 + ((S + 15) & ~15));
+    const unsigned g = (unsigned)std::min<uint64_t>((keys + 255) / 256, (uint64_t)sms * 16);
+    if (b->word == 8)
+        limits_kernel<uint64_t><<<g, 256, 0, s>>>((const uint64_t*)b->reps.p, D, (const uint32_t*)base,
+                                                  base + (S + 1) * 4, d_vlo, S, L, d_lim, keys);
+    else
+        limits_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, D, (const uint32_t*)base,
+                                                  base + (S + 1) * 4, d_vlo, S, L, d_lim, keys);
+    ED_CUDA(cudaGetLastError());
+    ED_CUDA(cudaStreamSynchronize(s));
+    b->n_keys = keys;
+    return ED_OK;
+}
+
+}  // namespace ed

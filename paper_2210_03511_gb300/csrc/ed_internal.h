@@ -1,0 +1,137 @@
+// Internal declarations of libed (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "ed.h"
+
+namespace ed {
+
+// ---------------------------------------------------------------- errors
+void set_error(ed_status st, const char* fmt, ...);
+ed_status fail(ed_status st, const char* fmt, ...);
+ed_status cuda_fail(cudaError_t e, const char* what);
+
+#define ED_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) return ed::cuda_fail(_e, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------- memory
+struct Alloc {
+    ed_allocator a{};
+    bool custom = false;
+    void* get(size_t bytes, cudaStream_t s) const;
+    void put(void* p, size_t bytes, cudaStream_t s) const;
+};
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// ---------------------------------------------------------------- sublattice-coding tables (host)
+// Table layouts (m = bits per sublattice block, S = 2^m substates):
+//   rep[X*S + s]                 Rep_X(s)                      (Eq. sublatrepdef)
+//   sym_off[X*(S+1) + s .. +1]   range of Sym_X(s) in sym_ids  (Eq. repsymdef)
+//   sa[(g*n_sub + X)*S + s]      SymmetryAction_X(g, s) as an m-bit substate of
+//                                block dest[g*n_sub + X]       (Eq. symactiondef)
+//   src[g*n_sub + Z]             the block X with dest(g, X) = Z
+struct HostTables {
+    int N = 0, n_up = 0, G = 0, n_sub = 0, m = 0;
+    std::vector<int32_t> perm;      // [G][N]
+    std::vector<uint8_t> flip;      // [G]
+    std::vector<double> chi;        // [G][2]
+    std::vector<uint8_t> dest, src; // [G][n_sub]
+    std::vector<uint16_t> rep;      // [n_sub][S]
+    std::vector<uint32_t> sym_off;  // [n_sub][S+1]
+    std::vector<uint16_t> sym_ids;
+    std::vector<uint16_t> sa;       // [G][n_sub][S]
+    std::vector<uint8_t> chi_one;   // [G] chi(g) == 1
+    bool real_chars = true;
+};
+
+ed_status build_host_tables(const ed_sector* sec, HostTables& t);
+
+// Device copy of the tables, in the order they are staged into shared memory.
+struct DevTables {
+    int N, G, n_sub, m;
+    int sa_bytes;            // 1 (m <= 8) or 2
+    const uint8_t* blob;     // contiguous device image (see tables_blob layout)
+    size_t blob_bytes;
+    // offsets (bytes) inside the blob
+    uint32_t off_rep, off_symoff, off_symids, off_sa, off_src, off_chi, off_chione, off_sqrt;
+    uint32_t off_chif, off_sqrtf;   // float copies of chi and sqrt tables for FP32 vectors
+};
+
+// ---------------------------------------------------------------- flip terms (host + device)
+// Off-diagonal non-branching terms grouped by site pair (a, b):
+//   h(sigma) = jhalf + i * sum_t k_t * s^z_{c_t} * (spin a down ? +1 : -1)
+// where jhalf = sum of J/2 over the bonds on {a,b} (exchange part of S_a.S_b)
+// and each chirality triangle containing the pair contributes k = +-Jchi/2
+// (sign + when (a, b, c) is a cyclic rotation of the triangle's order).
+struct FlipTerm {
+    int8_t pa, pb;   // bit positions (N-1-site)
+    int8_t pc0, pc1; // bit positions of the third sites, -1 if absent
+    float pad;
+    double jhalf;
+    double k0, k1;
+};
+
+struct DiagClass {          // Ising part grouped by coupling: sum_b J_b s^z_i s^z_j
+    double J;               // coupling of this class
+    int first, count;       // range in the bond-position list
+};
+
+}  // namespace ed
+
+// ---------------------------------------------------------------- opaque handles
+struct ed_basis {
+    ed::Alloc alloc;
+    ed::HostTables ht;
+    ed::DevTables dt{};
+    ed::DevBuf tables;          // blob
+    int64_t dim = 0;
+    int word = 4;               // bytes per state word (4 if N <= 32 else 8)
+    ed::DevBuf reps;            // [dim] uint32 or uint64, ascending
+    ed::DevBuf stab;            // [dim] uint16
+    int prefix_bits = 0;        // L = N - m: bits below the top sublattice block
+    // Two-level Limits directory, one device allocation:
+    //   base[S+1] (uint32): first key of top-block value v
+    //   q[S] (uint8, padded to 16 bytes): bucket bits used below the top block for v
+    //   limits[n_keys+1] (uint32): first basis index of each bucket
+    ed::DevBuf limits;
+    uint64_t n_keys = 0;
+    int device = 0;
+    size_t dir_q_off() const { return (size_t)((1 << ht.m) + 1) * 4; }
+    size_t dir_lim_off() const { return dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15); }
+};
+
+struct ed_hamiltonian {
+    const ed_basis* basis = nullptr;
+    bool is_real = true;
+    int n_flip = 0;
+    int n_diag_bonds = 0;
+    std::vector<ed::FlipTerm> flips;
+    std::vector<int8_t> diag_pos;       // [2*n_diag_bonds] bit positions
+    std::vector<ed::DiagClass> diag_cls;
+    ed::DevBuf d_flips, d_diag_pos, d_diag_cls, d_counters;
+    int n_diag_cls = 0;
+};
+
+namespace ed {
+// implemented in ed_basis.cu
+ed_status basis_build_device(ed_basis* b, cudaStream_t s);
+ed_status upload_tables(ed_basis* b, cudaStream_t s);
+// implemented in ed_apply.cu
+ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
+size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype dt);
+// implemented in ed_lanczos.cu
+ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
+                      ed_lanczos_report* rep, cudaStream_t s);
+}  // namespace ed

@@ -1,0 +1,472 @@
+// Lanczos eigensolver on the device (Eqs. lanczosrecursionabbrev, tmatrix;
+// Algs. "Real-symmetric Lanczos step" and "Complex-Hermitian Lanczos step").
+//
+// Per step: w = H v_n; alpha_n = Re<v_n|w>; w -= alpha_n v_n + beta_n v_{n-1};
+// optionally full reorthogonalisation against all stored v (classical
+// Gram-Schmidt, twice); beta_{n+1} = ||w||; v_{n+1} = w / beta_{n+1}.
+// Vectors are stored in the caller's dtype; every inner product accumulates
+// in FP64 with a fixed reduction tree (deterministic).  alpha and beta stay on
+// the device for the vector updates and are copied to the host for the
+// T-matrix, whose lowest eigenpairs are found in FP64 by Sturm bisection and
+// inverse iteration.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <vector>
+
+#include "ed_internal.h"
+
+namespace ed {
+
+template <int K> struct LV;
+template <> struct LV<0> { using T = double; static constexpr bool cplx = false; };
+template <> struct LV<1> { using T = float; static constexpr bool cplx = false; };
+template <> struct LV<2> { using T = double2; static constexpr bool cplx = true; };
+template <> struct LV<3> { using T = float2; static constexpr bool cplx = true; };
+
+__device__ __forceinline__ double2 ld2(const double& v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ double2 ld2(const float& v) { return make_double2((double)v, 0.0); }
+__device__ __forceinline__ double2 ld2(const double2& v) { return v; }
+__device__ __forceinline__ double2 ld2(const float2& v) { return make_double2((double)v.x, (double)v.y); }
+__device__ __forceinline__ void st2(double& d, double2 v) { d = v.x; }
+__device__ __forceinline__ void st2(float& d, double2 v) { d = (float)v.x; }
+__device__ __forceinline__ void st2(double2& d, double2 v) { d = v; }
+__device__ __forceinline__ void st2(float2& d, double2 v) { d = make_float2((float)v.x, (float)v.y); }
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) keyed by the state integer.
+__device__ __forceinline__ uint64_t smix(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double keyed_u(uint64_t seed, int stream, uint64_t state) {
+    const uint64_t key = smix(seed * 256ull + (uint64_t)stream);
+    return (double)(smix(state ^ key) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+template <typename W, int K>
+__global__ void init_random(typename LV<K>::T* v, const W* reps, int64_t n, uint64_t seed) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t st = (uint64_t)reps[i];
+        double2 z = make_double2(2.0 * keyed_u(seed, 0, st) - 1.0, LV<K>::cplx ? 2.0 * keyed_u(seed, 1, st) - 1.0 : 0.0);
+        st2(v[i], z);
+    }
+}
+
+__device__ __forceinline__ double2 block_sum2(double2 v) {
+    __shared__ double2 red[32];
+    for (int o = 16; o > 0; o >>= 1) {
+        v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+        v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+    }
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : make_double2(0, 0);
+        for (int o = 16; o > 0; o >>= 1) {
+            v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+            v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+        }
+    }
+    return v;  // valid in thread 0
+}
+
+// partial[blockIdx.y * gridDim.x + blockIdx.x] = sum_i conj(A_k[i]) b[i] over this block's slice
+template <int K>
+__global__ void multi_dot(const typename LV<K>::T* A, int64_t ld, const typename LV<K>::T* b, int64_t n,
+                          double2* partial) {
+    const typename LV<K>::T* a = A + (int64_t)blockIdx.y * ld;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n, i0 + per);
+    double2 acc = make_double2(0, 0);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const double2 x = ld2(a[i]), y = ld2(b[i]);
+        acc.x += x.x * y.x + x.y * y.y;
+        acc.y += x.x * y.y - x.y * y.x;
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// out[k] = sum over nb partials (fixed order)
+__global__ void reduce_partials(const double2* partial, int nb, int nk, double2* out) {
+    for (int k = blockIdx.x; k < nk; k += gridDim.x) {
+        double2 acc = make_double2(0, 0);
+        for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+            acc.x += partial[(int64_t)k * nb + i].x;
+            acc.y += partial[(int64_t)k * nb + i].y;
+        }
+        acc = block_sum2(acc);
+        if (threadIdx.x == 0) out[k] = acc;
+    }
+}
+
+// w -= alpha v + beta vprev  (alpha = Re sc[0], beta = sc[1].x; vprev may be null)
+template <int K>
+__global__ void lanczos_axpy(typename LV<K>::T* w, const typename LV<K>::T* v, const typename LV<K>::T* vp, int64_t n,
+                             const double2* alpha, const double* beta) {
+    const double a = alpha->x;
+    const double bt = vp ? *beta : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 x = ld2(w[i]);
+        const double2 y = ld2(v[i]);
+        x.x -= a * y.x;
+        x.y -= a * y.y;
+        if (vp) {
+            const double2 z = ld2(vp[i]);
+            x.x -= bt * z.x;
+            x.y -= bt * z.y;
+        }
+        st2(w[i], x);
+    }
+}
+
+// w -= sum_k c_k A_k  (classical Gram-Schmidt update)
+template <int K>
+__global__ void multi_axpy(typename LV<K>::T* w, const typename LV<K>::T* A, int64_t ld, int nk, const double2* c,
+                           int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 x = ld2(w[i]);
+        for (int k = 0; k < nk; ++k) {
+            const double2 a = ld2(A[(int64_t)k * ld + i]);
+            const double2 ck = c[k];
+            x.x -= ck.x * a.x - ck.y * a.y;
+            x.y -= ck.x * a.y + ck.y * a.x;
+        }
+        st2(w[i], x);
+    }
+}
+
+// out = sum_k s_k A_k with real coefficients s (FP64 accumulation, output type O)
+template <int K, typename O>
+__global__ void combine(O* out, const typename LV<K>::T* A, int64_t ld, int nk, const double* s, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 x = make_double2(0, 0);
+        for (int k = 0; k < nk; ++k) {
+            const double2 a = ld2(A[(int64_t)k * ld + i]);
+            x.x += s[k] * a.x;
+            x.y += s[k] * a.y;
+        }
+        st2(out[i], x);
+    }
+}
+
+// dst = src * (1/norm), norm = sqrt(Re nrm2->x) unless given as beta
+template <int K>
+__global__ void scale_by(typename LV<K>::T* dst, const typename LV<K>::T* src, int64_t n, const double* beta) {
+    const double inv = 1.0 / *beta;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 x = ld2(src[i]);
+        x.x *= inv;
+        x.y *= inv;
+        st2(dst[i], x);
+    }
+}
+
+__global__ void sqrt_re(const double2* in, double* out) { *out = sqrt(in->x); }
+
+// r = Hy - E y ; FP64 vectors of kind K (0 or 2)
+template <int K>
+__global__ void residual(typename LV<K>::T* r, const typename LV<K>::T* hy, const typename LV<K>::T* y, int64_t n,
+                         double E) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 a = ld2(hy[i]);
+        const double2 b = ld2(y[i]);
+        a.x -= E * b.x;
+        a.y -= E * b.y;
+        st2(r[i], a);
+    }
+}
+
+// ---------------------------------------------------------------- host tridiagonal eigensolver
+// Number of eigenvalues of T (diag a, off-diag b) smaller than x (Sturm count
+// from the pivots of the LDL^T factorisation of T - x).
+static int sturm_count(const std::vector<double>& a, const std::vector<double>& b, int n, double x) {
+    int cnt = 0;
+    double q = a[0] - x;
+    const double tiny = 1e-300;
+    if (q < 0) ++cnt;
+    for (int i = 1; i < n; ++i) {
+        if (q == 0.0) q = tiny;
+        q = (a[i] - x) - b[i - 1] * b[i - 1] / q;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+static double kth_eig(const std::vector<double>& a, const std::vector<double>& b, int n, int k) {
+    double lo = a[0], hi = a[0];
+    for (int i = 0; i < n; ++i) {
+        const double r = (i > 0 ? fabs(b[i - 1]) : 0.0) + (i < n - 1 ? fabs(b[i]) : 0.0);
+        lo = std::min(lo, a[i] - r);
+        hi = std::max(hi, a[i] + r);
+    }
+    for (int it = 0; it < 200; ++it) {
+        const double mid = 0.5 * (lo + hi);
+        if (mid <= lo || mid >= hi) break;
+        if (sturm_count(a, b, n, mid) > k) hi = mid;
+        else lo = mid;
+    }
+    return 0.5 * (lo + hi);
+}
+
+// Solve (T - lam) z = rhs by Gaussian elimination with partial pivoting on the
+// tridiagonal band (one extra superdiagonal appears from row swaps).
+static void tri_solve(const std::vector<double>& a, const std::vector<double>& b, int n, double lam,
+                      std::vector<double>& z) {
+    std::vector<double> dl(n), d(n), du(n), du2(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        d[i] = a[i] - lam;
+        dl[i] = i < n - 1 ? b[i] : 0.0;
+        du[i] = i < n - 1 ? b[i] : 0.0;
+    }
+    const double tiny = 1e-300 + 1e-15 * (fabs(lam) + 1.0) * 1e-3;
+    for (int i = 0; i < n - 1; ++i) {
+        if (fabs(d[i]) >= fabs(dl[i])) {
+            if (d[i] == 0.0) d[i] = tiny;
+            const double f = dl[i] / d[i];
+            d[i + 1] -= f * du[i];
+            z[i + 1] -= f * z[i];
+            dl[i] = 0.0;
+        } else {
+            // swap rows i and i+1
+            const double f = d[i] / dl[i];
+            d[i] = dl[i];
+            const double t = d[i + 1];
+            d[i + 1] = du[i] - f * t;
+            if (i < n - 2) {
+                du2[i] = du[i + 1];
+                du[i + 1] = -f * du2[i];
+            }
+            du[i] = t;
+            std::swap(z[i], z[i + 1]);
+            z[i + 1] -= f * z[i];
+            dl[i] = 0.0;
+        }
+    }
+    if (d[n - 1] == 0.0) d[n - 1] = tiny;
+    z[n - 1] /= d[n - 1];
+    if (n > 1) z[n - 2] = (z[n - 2] - du[n - 2] * z[n - 1]) / d[n - 2];
+    for (int i = n - 3; i >= 0; --i) z[i] = (z[i] - du[i] * z[i + 1] - du2[i] * z[i + 2]) / d[i];
+}
+
+// Lowest k eigenpairs of the n x n T-matrix.
+static void tri_eig(const std::vector<double>& a, const std::vector<double>& b, int n, int k, std::vector<double>& lam,
+                    std::vector<std::vector<double>>& vec) {
+    k = std::min(k, n);
+    lam.assign(k, 0.0);
+    vec.assign(k, std::vector<double>(n, 0.0));
+    for (int j = 0; j < k; ++j) {
+        lam[j] = kth_eig(a, b, n, j);
+        std::vector<double>& z = vec[j];
+        for (int i = 0; i < n; ++i) z[i] = 1.0 + 0.01 * ((i * 7919 + 13 * j) % 101);
+        for (int it = 0; it < 3; ++it) {
+            tri_solve(a, b, n, lam[j], z);
+            // keep orthogonal to earlier vectors of (near-)equal eigenvalues
+            for (int p = 0; p < j; ++p) {
+                if (fabs(lam[p] - lam[j]) > 1e-10 * (1.0 + fabs(lam[j]))) continue;
+                double dp = 0;
+                for (int i = 0; i < n; ++i) dp += z[i] * vec[p][i];
+                for (int i = 0; i < n; ++i) z[i] -= dp * vec[p][i];
+            }
+            double nr = 0;
+            for (int i = 0; i < n; ++i) nr += z[i] * z[i];
+            nr = sqrt(nr);
+            if (nr == 0.0) break;
+            for (int i = 0; i < n; ++i) z[i] /= nr;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- driver
+template <int K>
+struct Lz {
+    using T = typename LV<K>::T;
+    const ed_hamiltonian* h;
+    const ed_basis* b;
+    cudaStream_t s;
+    int64_t D;
+    int sms;
+    int nb;  // reduction blocks per vector
+    std::vector<std::pair<void*, size_t>> bufs;
+    ~Lz() {
+        cudaStreamSynchronize(s);
+        for (auto& p : bufs) b->alloc.put(p.first, p.second, s);
+    }
+    void* get(size_t n) {
+        void* p = b->alloc.get(n, s);
+        if (p) bufs.push_back({p, n});
+        return p;
+    }
+    unsigned grid() const { return (unsigned)std::min<int64_t>((D + 255) / 256, (int64_t)sms * 8); }
+};
+
+static int dtype_kind(ed_dtype d) { return d == ED_F64 ? 0 : d == ED_F32 ? 1 : d == ED_C128 ? 2 : 3; }
+
+template <int K>
+static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
+                     ed_lanczos_report* rep, cudaStream_t s) {
+    using T = typename LV<K>::T;
+    auto t0 = std::chrono::steady_clock::now();
+    Lz<K> z;
+    z.h = h;
+    z.b = h->basis;
+    z.s = s;
+    z.D = h->basis->dim;
+    ED_CUDA(cudaDeviceGetAttribute(&z.sms, cudaDevAttrMultiProcessorCount, h->basis->device));
+    const int64_t D = z.D;
+    z.nb = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (D + 4095) / 4096));
+    const int max_it = (int)std::min<int64_t>(o->max_iter, D);
+    const int n_eig = std::min<int>(o->n_eig, (int)D);
+    const int nstore = o->reorth ? max_it + 1 : 3;
+    T* V = (T*)z.get((size_t)nstore * D * sizeof(T));
+    T* w = (T*)z.get((size_t)D * sizeof(T));
+    double2* partial = (double2*)z.get((size_t)(max_it + 2) * z.nb * sizeof(double2));
+    double2* coef = (double2*)z.get((size_t)(max_it + 2) * sizeof(double2));
+    double* beta_d = (double*)z.get(2 * sizeof(double));
+    double2* alpha_d = (double2*)z.get(sizeof(double2));
+    if (!V || !w || !partial || !coef || !beta_d || !alpha_d) return fail(ED_ERR_NOMEM, "Lanczos workspace");
+    const unsigned g = z.grid();
+    auto vec = [&](int k) -> T* { return V + (int64_t)(o->reorth ? k : (k % 3)) * D; };
+    auto dot = [&](const T* A, int nk, const T* bv, double2* out) {
+        multi_dot<K><<<dim3(z.nb, nk), 256, 0, s>>>(A, D, bv, D, partial);
+        reduce_partials<<<std::min(nk, 1024), 256, 0, s>>>(partial, z.nb, nk, out);
+    };
+    // v_1: keyed random, normalised
+    if (h->basis->word == 8) init_random<uint64_t, K><<<g, 256, 0, s>>>(vec(0), (const uint64_t*)h->basis->reps.p, D, o->seed);
+    else init_random<uint32_t, K><<<g, 256, 0, s>>>(vec(0), (const uint32_t*)h->basis->reps.p, D, o->seed);
+    dot(vec(0), 1, vec(0), coef);
+    sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
+    scale_by<K><<<g, 256, 0, s>>>(vec(0), vec(0), D, beta_d);
+    ED_CUDA(cudaGetLastError());
+    std::vector<double> al, be;  // al[n] = alpha_n, be[n] = beta_{n+1}
+    std::vector<double> prev(n_eig, 0.0), lam;
+    std::vector<std::vector<double>> svec;
+    int n_apply = 0, iters = 0;
+    bool conv = false;
+    const int every = std::max(1, o->check_every);
+    ed_dtype vdt = o->dtype;
+    for (int n = 0; n < max_it; ++n) {
+        ed_status st = apply_launch(h, vdt, vec(n), w, 1, s);
+        if (st != ED_OK) return st;
+        ++n_apply;
+        dot(vec(n), 1, w, alpha_d);
+        // beta_d still holds beta_n from the previous step
+        lanczos_axpy<K><<<g, 256, 0, s>>>(w, vec(n), n > 0 ? vec(n - 1) : nullptr, D, alpha_d, beta_d);
+        if (o->reorth) {
+            for (int pass = 0; pass < 2; ++pass) {
+                dot(V, n + 1, w, coef);
+                multi_axpy<K><<<g, 256, 0, s>>>(w, V, D, n + 1, coef, D);
+            }
+        }
+        dot(w, 1, w, coef + n + 1);
+        sqrt_re<<<1, 1, 0, s>>>(coef + n + 1, beta_d);
+        double2 ah;
+        double bh;
+        ED_CUDA(cudaMemcpyAsync(&ah, alpha_d, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaMemcpyAsync(&bh, beta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        al.push_back(ah.x);
+        be.push_back(bh);
+        iters = n + 1;
+        const double tnorm = fabs(ah.x) + bh + 1e-300;
+        const bool breakdown = bh < 1e-13 * tnorm;
+        const bool last = breakdown || n + 1 == max_it;
+        if ((n + 1) % every == 0 || last) {
+            tri_eig(al, be, iters, n_eig, lam, svec);
+            bool ok = (int)lam.size() == n_eig || breakdown;
+            for (int k = 0; k < (int)lam.size() && ok; ++k) {
+                const double sc = std::max(1.0, fabs(lam[k]));
+                const double rb = bh * fabs(svec[k][iters - 1]);
+                double gap = 1e300;
+                for (int p = 0; p < (int)lam.size(); ++p)
+                    if (p != k) gap = std::min(gap, fabs(lam[p] - lam[k]));
+                if (n_eig == 1 && iters > 1) {
+                    std::vector<double> l2;
+                    std::vector<std::vector<double>> s2;
+                    tri_eig(al, be, iters, 2, l2, s2);
+                    if (l2.size() > 1) gap = l2[1] - l2[0];
+                }
+                const bool steady = fabs(lam[k] - prev[k]) <= o->tol * sc;
+                const bool small_res = rb * rb / std::max(gap, 1e-12) <= o->tol * sc || rb <= o->tol * sc;
+                if (!(steady && small_res) && !breakdown) ok = false;
+            }
+            for (int k = 0; k < (int)lam.size(); ++k) prev[k] = lam[k];
+            if (ok) conv = true;
+        }
+        if (conv || last) break;
+        scale_by<K><<<g, 256, 0, s>>>(vec(n + 1), w, D, beta_d);
+    }
+    ED_CUDA(cudaGetLastError());
+    const int nk = (int)lam.size();
+    ed_lanczos_report r{};
+    r.iters = iters;
+    r.converged = conv ? 1 : 0;
+    for (int k = nk; k < o->n_eig; ++k) evals[k] = NAN;
+    for (int k = 0; k < nk && k < 8; ++k) {
+        r.ritz[k] = lam[k];
+        r.resid_bound[k] = be[iters - 1] * fabs(svec[k][iters - 1]);
+        evals[k] = lam[k];
+    }
+    // Ritz vectors (need stored Lanczos vectors)
+    const bool mixed = (K == 1 || K == 3);
+    if (o->reorth && (evecs || (mixed && o->refine))) {
+        double* sd = (double*)z.get((size_t)iters * sizeof(double));
+        if (!sd) return fail(ED_ERR_NOMEM, "Ritz workspace");
+        const int K64 = LV<K>::cplx ? 2 : 0;
+        using T64 = typename LV<(LV<K>::cplx ? 2 : 0)>::T;
+        T64* y64 = (mixed && o->refine) ? (T64*)z.get((size_t)D * sizeof(T64)) : nullptr;
+        T64* hy64 = (mixed && o->refine) ? (T64*)z.get((size_t)D * sizeof(T64)) : nullptr;
+        double2* d2 = (double2*)z.get(2 * sizeof(double2));
+        if (mixed && o->refine && (!y64 || !hy64 || !d2)) return fail(ED_ERR_NOMEM, "refinement workspace");
+        for (int k = 0; k < nk; ++k) {
+            ED_CUDA(cudaMemcpyAsync(sd, svec[k].data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
+            if (evecs) combine<K, T><<<g, 256, 0, s>>>((T*)evecs + (int64_t)k * D, V, D, iters, sd, D);
+            if (mixed && o->refine) {
+                combine<K, T64><<<g, 256, 0, s>>>(y64, V, D, iters, sd, D);
+                ed_status st = apply_launch(h, K64 == 2 ? ED_C128 : ED_F64, y64, hy64, 1, s);
+                if (st != ED_OK) return st;
+                ++n_apply;
+                // E = <y|Hy>/<y|y>, residual ||Hy - E y|| / ||y||
+                multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(y64, D, hy64, D, partial);
+                reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, d2);
+                multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(y64, D, y64, D, partial);
+                reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, d2 + 1);
+                double2 hh[2];
+                ED_CUDA(cudaMemcpyAsync(hh, d2, sizeof hh, cudaMemcpyDeviceToHost, s));
+                ED_CUDA(cudaStreamSynchronize(s));
+                const double E = hh[0].x / hh[1].x;
+                residual<K64><<<g, 256, 0, s>>>(hy64, hy64, y64, D, E);
+                multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(hy64, D, hy64, D, partial);
+                reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, d2);
+                ED_CUDA(cudaMemcpyAsync(hh, d2, sizeof(double2), cudaMemcpyDeviceToHost, s));
+                ED_CUDA(cudaStreamSynchronize(s));
+                r.refined[k] = E;
+                r.refined_resid[k] = sqrt(hh[0].x / hh[1].x);
+                evals[k] = E;
+            }
+        }
+        ED_CUDA(cudaGetLastError());
+    }
+    ED_CUDA(cudaStreamSynchronize(s));
+    r.n_apply = n_apply;
+    r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (rep) *rep = r;
+    return conv ? ED_OK : fail(ED_ERR_NOT_CONVERGED, "Lanczos did not converge in %d steps", iters);
+}
+
+ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
+                      ed_lanczos_report* rep, cudaStream_t s) {
+    switch (dtype_kind(o->dtype)) {
+        case 0: return run<0>(h, o, evals, evecs, rep, s);
+        case 1: return run<1>(h, o, evals, evecs, rep, s);
+        case 2: return run<2>(h, o, evals, evecs, rep, s);
+        default: return run<3>(h, o, evals, evecs, rep, s);
+    }
+}
+
+}  // namespace ed

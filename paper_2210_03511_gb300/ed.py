@@ -1,0 +1,243 @@
+"""Thin Python binding of libed (argument marshalling only).
+
+Every computation runs in libed's CUDA kernels; this module converts numpy /
+torch arguments to the C structs of include/ed.h and back.  It never falls
+back to a CPU implementation: if libed.so is missing it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libed.so")
+
+ED_F64, ED_F32, ED_C64, ED_C128 = 0, 1, 2, 3
+STATUS = ["ED_OK", "ED_ERR_ARG", "ED_ERR_NOT_GROUP", "ED_ERR_NOT_SYMMETRIC", "ED_ERR_NOT_SUBLATTICE_STABLE",
+          "ED_ERR_CHAR_NOT_HOMOMORPHISM", "ED_ERR_SPINFLIP_SZ", "ED_ERR_EMPTY_SECTOR", "ED_ERR_NOMEM",
+          "ED_ERR_INDEX_NOT_FOUND", "ED_ERR_TIMEOUT", "ED_ERR_NOT_CONVERGED", "ED_ERR_CUDA", "ED_ERR_TABLE_TOO_LARGE"]
+
+P = ctypes.POINTER
+c_i32, c_i64, c_u8, c_u16, c_u32, c_u64, c_dbl, c_vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint8,
+                                                         ctypes.c_uint16, ctypes.c_uint32, ctypes.c_uint64,
+                                                         ctypes.c_double, ctypes.c_void_p)
+
+
+class EdError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        self.name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{self.name}: {msg}")
+
+
+class ed_sector(ctypes.Structure):
+    _fields_ = [("n_sites", c_i32), ("n_up", c_i32), ("n_sym", c_i32), ("perm", P(c_i32)), ("spinflip", P(c_u8)),
+                ("chi", P(c_dbl)), ("n_sublat", c_i32)]
+
+
+class ed_terms(ctypes.Structure):
+    _fields_ = [("n_bonds", c_i32), ("bond", P(c_i32)), ("J", P(c_dbl)), ("n_tri", c_i32), ("tri", P(c_i32)),
+                ("Jchi", P(c_dbl))]
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(c_vp, ctypes.c_size_t, c_vp, c_vp)
+FREE_FN = ctypes.CFUNCTYPE(None, c_vp, ctypes.c_size_t, c_vp, c_vp)
+
+
+class ed_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", c_vp)]
+
+
+class ed_lanczos_opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("n_eig", c_i32), ("tol", c_dbl), ("max_iter", c_i32), ("reorth", c_i32),
+                ("seed", c_u64), ("refine", c_i32), ("check_every", c_i32)]
+
+
+class ed_lanczos_report(ctypes.Structure):
+    _fields_ = [("iters", c_i32), ("converged", c_i32), ("n_apply", c_i32), ("ritz", c_dbl * 8),
+                ("resid_bound", c_dbl * 8), ("refined", c_dbl * 8), ("refined_resid", c_dbl * 8),
+                ("seconds", c_dbl)]
+
+
+_lib = None
+
+
+def lib():
+    """Load libed.so (built in-tree by paper_2210_03511_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libed.so not built ({LIB_PATH}); run paper_2210_03511_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        L.ed_basis_build.argtypes = [P(ed_sector), P(ed_allocator), c_vp, P(c_vp)]
+        L.ed_basis_dim.argtypes = [c_vp, P(c_i64)]
+        L.ed_basis_export.argtypes = [c_vp, P(c_u64), P(c_u16)]
+        L.ed_sector_tables.argtypes = [P(ed_sector), P(c_u16), P(c_u32), P(c_u16), P(c_i64), P(c_u16), P(c_u8)]
+        L.ed_basis_free.argtypes = [c_vp]
+        L.ed_basis_free.restype = None
+        L.ed_hamiltonian_create.argtypes = [c_vp, P(ed_terms), P(c_vp)]
+        L.ed_hamiltonian_is_real.argtypes = [c_vp, P(c_i32)]
+        L.ed_hamiltonian_free.argtypes = [c_vp]
+        L.ed_hamiltonian_free.restype = None
+        L.ed_apply.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
+        L.ed_apply_counters.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
+        L.ed_lanczos.argtypes = [c_vp, P(ed_lanczos_opts), P(c_dbl), c_vp, P(ed_lanczos_report), c_vp]
+        L.ed_last_error.restype = ctypes.c_char_p
+        L.ed_version.restype = ctypes.c_char_p
+        for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
+                  "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_lanczos"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def check(status: int):
+    if status != 0:
+        raise EdError(status, lib().ed_last_error().decode())
+
+
+def _ptr(a: np.ndarray, ct):
+    return a.ctypes.data_as(P(ct))
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _sector_struct(sector):
+    perm = np.ascontiguousarray(sector.perm, dtype=np.int32)
+    flip = np.ascontiguousarray(sector.spinflip, dtype=np.uint8)
+    chi = np.asarray(sector.chi, dtype=complex)
+    chi2 = np.ascontiguousarray(np.stack([chi.real, chi.imag], axis=1), dtype=np.float64)
+    s = ed_sector(int(sector.n_sites), int(sector.n_up), int(len(perm)), _ptr(perm, c_i32), _ptr(flip, c_u8),
+                  _ptr(chi2, c_dbl), int(sector.n_sublat))
+    return s, [perm, flip, chi2]
+
+
+def sector_tables(sector) -> dict:
+    """ed_sector_tables: host-side validation and sublattice-coding tables (no GPU needed)."""
+    s, keep = _sector_struct(sector)
+    N, n_sub, G = int(sector.n_sites), int(sector.n_sublat), int(len(keep[0]))
+    m = N // n_sub if n_sub else 0
+    n = c_i64()
+    check(lib().ed_sector_tables(ctypes.byref(s), None, None, None, ctypes.byref(n), None, None))
+    S = 1 << m
+    rep = np.zeros(n_sub * S, np.uint16)
+    off = np.zeros(n_sub * (S + 1), np.uint32)
+    ids = np.zeros(max(n.value, 1), np.uint16)
+    sa = np.zeros(G * n_sub * S, np.uint16)
+    dest = np.zeros(G * n_sub, np.uint8)
+    check(lib().ed_sector_tables(ctypes.byref(s), _ptr(rep, c_u16), _ptr(off, c_u32), _ptr(ids, c_u16),
+                                 ctypes.byref(n), _ptr(sa, c_u16), _ptr(dest, c_u8)))
+    return dict(m=m, rep=rep.reshape(n_sub, S), sym_off=off.reshape(n_sub, S + 1), sym_ids=ids[:n.value],
+                sa=sa.reshape(G, n_sub, S), dest=dest.reshape(G, n_sub))
+
+
+class Basis:
+    """ed_basis_build / ed_basis_dim / ed_basis_export / ed_basis_free."""
+
+    def __init__(self, sector, stream=None):
+        self._sec, self._keep = _sector_struct(sector)
+        self.n_sites = int(sector.n_sites)
+        self.handle = c_vp()
+        check(lib().ed_basis_build(ctypes.byref(self._sec), None, _stream_handle(stream), ctypes.byref(self.handle)))
+        d = c_i64()
+        check(lib().ed_basis_dim(self.handle, ctypes.byref(d)))
+        self.dim = int(d.value)
+
+    def export(self):
+        reps = np.zeros(self.dim, dtype=np.uint64)
+        stab = np.zeros(self.dim, dtype=np.uint16)
+        check(lib().ed_basis_export(self.handle, _ptr(reps, c_u64), _ptr(stab, c_u16)))
+        return reps, stab
+
+    def close(self):
+        if self.handle:
+            lib().ed_basis_free(self.handle)
+            self.handle = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hamiltonian:
+    """ed_hamiltonian_create / ed_apply / ed_lanczos."""
+
+    def __init__(self, basis: Basis, terms):
+        self.basis = basis
+        bonds = np.ascontiguousarray(np.asarray(terms.bonds, dtype=np.int32).reshape(-1, 2))
+        J = np.ascontiguousarray(terms.J, dtype=np.float64)
+        tris = np.ascontiguousarray(np.asarray(terms.tris, dtype=np.int32).reshape(-1, 3))
+        Jc = np.ascontiguousarray(terms.Jchi, dtype=np.float64)
+        self._keep = [bonds, J, tris, Jc]
+        t = ed_terms(len(bonds), _ptr(bonds, c_i32), _ptr(J, c_dbl), len(tris), _ptr(tris, c_i32), _ptr(Jc, c_dbl))
+        self.handle = c_vp()
+        check(lib().ed_hamiltonian_create(basis.handle, ctypes.byref(t), ctypes.byref(self.handle)))
+        r = c_i32()
+        check(lib().ed_hamiltonian_is_real(self.handle, ctypes.byref(r)))
+        self.is_real = bool(r.value)
+
+    @property
+    def dim(self) -> int:
+        return self.basis.dim
+
+    def apply_ptr(self, dtype: int, x_ptr: int, y_ptr: int, nvec: int = 1, stream=None):
+        check(lib().ed_apply(self.handle, dtype, x_ptr, y_ptr, nvec, _stream_handle(stream)))
+
+    def apply(self, x, y, stream=None):
+        """y = H x for torch CUDA tensors of shape [D] or [nvec, D] (contiguous)."""
+        import torch
+        dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
+        if x.dtype != y.dtype or x.shape != y.shape or not x.is_cuda or not y.is_cuda:
+            raise ValueError("x and y must be CUDA tensors of the same dtype and shape")
+        if not (x.is_contiguous() and y.is_contiguous()) or x.shape[-1] != self.dim:
+            raise ValueError("x and y must be contiguous with last dimension = basis dimension")
+        nvec = 1 if x.dim() == 1 else x.shape[0]
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        self.apply_ptr(dt, x.data_ptr(), y.data_ptr(), nvec, stream)
+        return y
+
+    def counters(self, stream=None):
+        g = c_i64()
+        s = c_i64()
+        check(lib().ed_apply_counters(self.handle, _stream_handle(stream), ctypes.byref(g), ctypes.byref(s)))
+        return int(g.value), int(s.value)
+
+    def lanczos(self, n_eig=1, tol=1e-10, max_iter=300, dtype=None, reorth=True, seed=1, refine=False,
+                check_every=1, evecs=None, stream=None, raise_on_nonconv=True):
+        if dtype is None:
+            dtype = ED_F64 if self.is_real else ED_C128
+        o = ed_lanczos_opts(dtype, n_eig, tol, max_iter, int(reorth), seed, int(refine), check_every)
+        ev = (c_dbl * 8)()
+        rep = ed_lanczos_report()
+        ptr = evecs.data_ptr() if evecs is not None else None
+        st = lib().ed_lanczos(self.handle, ctypes.byref(o), ev, ptr, ctypes.byref(rep), _stream_handle(stream))
+        if st != 0 and not (st == 11 and not raise_on_nonconv):
+            check(st)
+        return np.array(ev[:n_eig]), rep
+
+    def close(self):
+        if self.handle:
+            lib().ed_hamiltonian_free(self.handle)
+            self.handle = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def report_dict(rep: ed_lanczos_report, n: int) -> dict:
+    return dict(iters=rep.iters, converged=bool(rep.converged), n_apply=rep.n_apply, ritz=list(rep.ritz[:n]),
+                resid_bound=list(rep.resid_bound[:n]), refined=list(rep.refined[:n]),
+                refined_resid=list(rep.refined_resid[:n]), seconds=rep.seconds)

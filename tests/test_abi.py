@@ -1,0 +1,156 @@
+"""C ABI checks that need no GPU: the library loads, exports every function of
+include/ed.h, validates sectors, and builds the sublattice-coding tables of
+Alg. "Preparation of lookup tables for sublattice coding algorithm" as the
+thesis's two worked examples state them."""
+import ctypes
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from edinputs import configs as C
+from edinputs.lattice import Sector
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2210_03511_gb300 import build
+    build.build()
+    import paper_2210_03511_gb300 as pkg
+    return pkg
+
+
+def test_exports_every_declared_function(P):
+    hdr = open(os.path.join(ROOT, "include", "ed.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    names = set(re.findall(r"\b(ed_[a-z_0-9]+)\s*\(", hdr))
+    assert {"ed_basis_build", "ed_apply", "ed_lanczos"} <= names
+    L = ctypes.CDLL(P.ed.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(L, n), n
+
+
+def _chain6(site_positions, chi=None, flip=None):
+    pos = list(site_positions)
+    site_of = {x: i for i, x in enumerate(pos)}
+    perm = np.array([[site_of[(pos[i] + n) % 6] for i in range(6)] for n in range(6)], dtype=np.int32)
+    chi = np.ones(6, complex) if chi is None else chi
+    flip = np.zeros(6, np.uint8) if flip is None else flip
+    return perm, chi, flip
+
+
+def _bits(s):
+    return int(s, 2)
+
+
+def _sym_set(t, X, s):
+    off = t["sym_off"]
+    return sorted(int(g) for g in t["sym_ids"][off[X, s]:off[X, s + 1]])
+
+
+def test_worked_example_two_sublattices(P):
+    """Tables of the two-sublattice example: G_A, G_B, Rep_A, Rep_B, Sym_B."""
+    ex = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_examples.json")))["two_sublattice"]
+    perm, chi, flip = _chain6(ex["site_positions"])
+    t = P.sector_tables(Sector(6, 3, perm, flip, chi, 2))
+    assert t["m"] == 3
+    # G_X = elements mapping block X onto block 0 (A)
+    GA = [g for g in range(6) if t["dest"][g, 0] == 0]
+    GB = [g for g in range(6) if t["dest"][g, 1] == 0]
+    name = lambda g: "Id" if g == 0 else f"T{g}"
+    assert [name(g) for g in GA] == ex["G_A"] and [name(g) for g in GB] == ex["G_B"]
+    sA, sB = _bits(ex["substate_A"]), _bits(ex["substate_B"])
+    assert t["rep"][0, sA] == ex["Rep_A"]
+    assert t["rep"][1, sB] == ex["Rep_B"]
+    assert [name(g) for g in _sym_set(t, 1, sB)] == ex["Sym_B"]
+
+
+def test_worked_example_three_sublattices(P):
+    """Tables of the three-sublattice example: Rep_A/B/C and Sym_A/B/C."""
+    ex = json.load(open(os.path.join(ROOT, "tests", "golden", "worked_examples.json")))["three_sublattice"]
+    perm, chi, flip = _chain6(ex["site_positions"])
+    t = P.sector_tables(Sector(6, 3, perm, flip, chi, 3))
+    name = lambda g: "Id" if g == 0 else f"T{g}"
+    for X, lab in enumerate("ABC"):
+        s = _bits(ex[f"substate_{lab}"])
+        assert t["rep"][X, s] == ex[f"Rep_{lab}"], lab
+        assert [name(g) for g in _sym_set(t, X, s)] == ex[f"Sym_{lab}"], lab
+    # SymmetryAction composes T2 sigma = 000111 block by block
+    st = _bits(ex["state"])
+    sub = [(st >> (2 * (2 - X))) & 3 for X in range(3)]
+    img = [0, 0, 0]
+    for X in range(3):
+        img[t["dest"][2, X]] = t["sa"][2, X, sub[X]]
+    assert (img[0] << 4) | (img[1] << 2) | img[2] == _bits(ex["T2_image"])
+
+
+def test_tables_match_definitions_bruteforce(P):
+    """Rep_X(s) = min over G_X of SymmetryAction_X(g, s); Sym_X(s) = its argmin set (Eqs. sublatrepdef, repsymdef)."""
+    p = C.square([[4, 0], [0, 4]], 1.0, 0.5, spinflip=1)
+    s = p.sector
+    t = P.sector_tables(s)
+    m, n_sub, G = t["m"], s.n_sublat, s.n_sym
+    N = s.n_sites
+    for X in range(n_sub):
+        for sub in range(1 << m):
+            vals = {}
+            for g in range(G):
+                Z = int(t["dest"][g, X])
+                # direct action on the full state restricted to block X
+                img = 0
+                for l in range(m):
+                    bit = (sub >> (m - 1 - l)) & 1
+                    if s.spinflip[g]:
+                        bit ^= 1
+                    if bit:
+                        img |= 1 << (m - 1 - (int(s.perm[g][X * m + l]) - Z * m))
+                assert t["sa"][g, X, sub] == img
+                if Z == 0:
+                    vals[g] = img
+            best = min(vals.values())
+            assert t["rep"][X, sub] == best
+            assert _sym_set(t, X, sub) == sorted(g for g, v in vals.items() if v == best)
+
+
+def test_validation_errors(P):
+    base = C.chain(8, translations=True)
+    s = base.sector
+
+    def err(sec):
+        with pytest.raises(P.EdError) as e:
+            P.sector_tables(sec)
+        return e.value.name
+
+    bad = Sector(s.n_sites, s.n_up, s.perm[::-1].copy(), s.spinflip, s.chi, s.n_sublat)
+    assert err(bad) == "ED_ERR_NOT_GROUP"  # identity not first
+    assert err(Sector(s.n_sites, s.n_up, s.perm[:3].copy(), s.spinflip[:3], s.chi[:3], s.n_sublat)) == "ED_ERR_NOT_GROUP"
+    chi = s.chi.copy()
+    chi[1] *= -1
+    assert err(Sector(s.n_sites, s.n_up, s.perm, s.spinflip, chi, s.n_sublat)) == "ED_ERR_CHAR_NOT_HOMOMORPHISM"
+    chi = s.chi.copy() * 1.1
+    chi[0] = 1
+    assert err(Sector(s.n_sites, s.n_up, s.perm, s.spinflip, chi, s.n_sublat)) == "ED_ERR_CHAR_NOT_HOMOMORPHISM"
+    pf = C.chain(8, translations=True, spinflip=1).sector
+    assert err(Sector(8, 3, pf.perm, pf.spinflip, pf.chi, pf.n_sublat)) == "ED_ERR_SPINFLIP_SZ"
+    # translations by one site split the 2-block partition {0..3},{4..7} of a chain numbered in order
+    perm = np.array([[(i + n) % 8 for i in range(8)] for n in range(8)], np.int32)
+    assert err(Sector(8, 4, perm, np.zeros(8, np.uint8), np.ones(8, complex), 2)) == "ED_ERR_NOT_SUBLATTICE_STABLE"
+    assert err(Sector(8, 4, perm, np.zeros(8, np.uint8), np.ones(8, complex), 3)) == "ED_ERR_ARG"
+    perm2 = perm.copy()
+    perm2[3] = perm2[2]
+    assert err(Sector(8, 4, perm2, np.zeros(8, np.uint8), np.ones(8, complex), 1)) == "ED_ERR_NOT_GROUP"
+    assert err(Sector(70, 35, np.arange(70, dtype=np.int32)[None], np.zeros(1, np.uint8), np.ones(1, complex), 1)) \
+        == "ED_ERR_ARG"
+
+
+def test_workload_tables_fit_shared_memory(P):
+    """SymmetryAction for the workloads stays below 96 KB (shared-memory staging)."""
+    for make in (C.square32, C.kagome36, C.triangular24, C.square40):
+        s = make().sector
+        t = P.sector_tables(s)
+        bytes_sa = s.n_sym * s.n_sublat * (1 << t["m"]) * (1 if t["m"] <= 8 else 2)
+        assert bytes_sa <= 96 * 1024
