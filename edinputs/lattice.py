@@ -526,16 +526,37 @@ def _stable(blocks, perm) -> bool:
     return True
 
 
-def choose_partition(cands, n_sym: int, max_table_bytes: int):
-    """Fewest sublattices whose SymmetryAction table (|G| x n_sub x 2^m bytes) fits the budget."""
+def _local_map_count(blocks, perm, flip) -> int:
+    """Distinct (local position map, flip) pairs induced on the blocks by the group."""
+    m = len(blocks[0])
+    N = sum(len(b) for b in blocks)
+    order = [i for b in blocks for i in b]
+    new_of_old = np.empty(N, dtype=np.int64)
+    new_of_old[order] = np.arange(N)
+    pn = new_of_old[perm[:, order]]
+    seen = set()
+    for g in range(len(pn)):
+        for X in range(len(blocks)):
+            Z = pn[g, X * m] // m
+            seen.add((tuple((pn[g, X * m:(X + 1) * m] - Z * m).tolist()), int(flip[g])))
+    return len(seen)
+
+
+def choose_partition(cands, perm, flip, max_table_bytes: int, max_block: int = 12):
+    """Fewest sublattices (largest blocks, fewest representative candidates) whose
+    SymmetryAction tables, stored once per distinct local map, fit the budget.
+
+    A map costs 2^m bytes for m <= 8, else two uint16 chunk tables of
+    2^(m - m//2) + 2^(m//2) entries."""
     best = None
     for blocks in cands:
         n_sub = len(blocks)
         m = len(blocks[0])
-        if m > 16:
+        if m > max_block:
             continue
-        eb = 1 if m <= 8 else 2
-        size = n_sym * n_sub * (1 << m) * eb
+        per_map = (1 << m) if m <= 8 else 2 * ((1 << (m - m // 2)) + (1 << (m // 2)))
+        n_map = _local_map_count(blocks, perm, flip)
+        size = n_map * per_map
         if size > max_table_bytes:
             continue
         key = (n_sub, size)
@@ -615,7 +636,7 @@ def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: i
     cands = sublattice_partitions(cl, sgk)
     if n_sublat is not None:
         cands = [c for c in cands if len(c) == n_sublat]
-    blocks = choose_partition(cands, len(perm), max_table_bytes)
+    blocks = choose_partition(cands, perm, flip, max_table_bytes)
     order = [i for b in blocks for i in b]         # new site -> old site
     new_of_old = np.empty(N, dtype=np.int64)
     new_of_old[order] = np.arange(N)

@@ -142,6 +142,17 @@ ed_status ed_basis_export(const ed_basis* basis, uint64_t* reps, uint16_t* stab)
 ed_status ed_sector_tables(const ed_sector* sector, uint16_t* rep, uint32_t* sym_off, uint16_t* sym_ids,
                            int64_t* n_sym_ids, uint16_t* sa, uint8_t* dest);
 
+/* ed_representatives -- Alg. "Sublattice coding algorithm for finding the
+ * representative" on the device for n caller-given states (HOST arrays, any
+ * popcount; bits above n_sites are ignored).  Validates the sector like
+ * ed_basis_build and uploads its tables for the duration of the call; n_up is
+ * not used.  Outputs (HOST, any may be NULL): rep[n] the orbit minimum, g[n]
+ * one element with g.state = rep, nstab[n] = |Stab(rep)|, compat[n] = 1 if the
+ * representative's projector is non-zero in this sector.  Synchronous;
+ * device memory from cudaMalloc, released before return. */
+ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
+                             int32_t* nstab, uint8_t* compat);
+
 void ed_basis_free(ed_basis* basis);
 
 /* ed_hamiltonian_create -- bind terms to a basis.
@@ -181,11 +192,13 @@ ed_status ed_apply_counters(const ed_hamiltonian* h, ed_stream stream, int64_t* 
 typedef struct {
     ed_dtype dtype;        /* vector type: F64/C128 plain, F32/C64 mixed (FP64 reductions) */
     int32_t n_eig;         /* lowest eigenvalues wanted, 1..8 */
-    double tol;            /* convergence tolerance on eigenvalues (relative, e.g. 1e-10) */
+    double tol;            /* convergence tolerance on eigenvalues (relative, e.g. 1e-10); with F32/C64
+                              vectors the FP32 phase stops at max(tol, 1e-6) and tol applies to the refinement */
     int32_t max_iter;      /* Lanczos steps at most (<= 2000) */
     int32_t reorth;        /* 1 = full reorthogonalisation (classical Gram-Schmidt twice) against stored vectors */
     uint64_t seed;         /* start vector v1(state) = keyed SplitMix64 uniform in [-1,1), normalised */
-    int32_t refine;        /* mixed precision: FP64 H.x applications for the Rayleigh quotient of the Ritz vectors */
+    int32_t refine;        /* mixed precision (F32/C64): at most this many FP64 Lanczos steps, started from the
+                              FP32 Ritz vectors, refine the eigenvalues (0 = no refinement) */
     int32_t check_every;   /* T-matrix eigensolve every this many steps (>= 1) */
 } ed_lanczos_opts;
 
@@ -195,8 +208,8 @@ typedef struct {
     int32_t n_apply;           /* H.x applications (including refinement) */
     double ritz[8];            /* T-matrix eigenvalues at exit (in the vector dtype's precision) */
     double resid_bound[8];     /* beta_n |s_n,k|: Lanczos residual bound of each Ritz pair */
-    double refined[8];         /* FP64 Rayleigh quotients of the Ritz vectors (when refine) */
-    double refined_resid[8];   /* FP64 ||H v - E v|| of the normalised Ritz vectors (when refine) */
+    double refined[8];         /* eigenvalues after the FP64 refinement (when refine) */
+    double refined_resid[8];   /* FP64 Lanczos residual bounds of the refined eigenpairs (when refine) */
     double seconds;            /* wall time of the call */
 } ed_lanczos_report;
 
@@ -205,7 +218,10 @@ typedef struct {
  * and "Complex-Hermitian Lanczos step") with FP64 inner products,
  * optional full reorthogonalisation, and the tridiagonal eigenproblem solved in
  * FP64 every check_every steps.  evals: HOST [n_eig] (refined values when
- * opts.refine, else Ritz values).  evecs: DEVICE [n_eig][D] of the vector dtype,
+ * opts.refine and the vectors are FP32, else Ritz values).  Converged means,
+ * for each wanted Ritz value theta, |theta_n - theta_{n-c}| <= tol max(1,|theta|)
+ * between checks and a Lanczos residual bound r = beta |s_last| with
+ * min(r, r^2/gap) <= tol max(1,|theta|).  evecs: DEVICE [n_eig][D] of the vector dtype,
  * or NULL (needs reorth = 1 to be filled).  Workspace comes from cudaMalloc
  * and is released before return.  Synchronous.  Returns
  * ED_ERR_NOT_CONVERGED if max_iter is reached first (results still written). */

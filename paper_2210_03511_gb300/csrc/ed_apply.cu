@@ -54,8 +54,8 @@ __device__ __forceinline__ R warp_sum(R v) {
     return v;
 }
 
-template <typename W, typename SAT, int K>
-__global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
+template <typename W, bool CH, int K, int NV>
+__global__ void __launch_bounds__(1024, 1) hx_kernel(HxArgs a) {
     using V = Val<K>;
     using T = typename V::T;
     using R = typename V::R;
@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
     for (int i = threadIdx.x; i <= a.S; i += blockDim.x) dir_base[i] = a.dir_base[i];
     for (int i = threadIdx.x; i < a.S; i += blockDim.x) dir_q[i] = a.dir_q[i];
     __syncthreads();
-    const TabView<SAT> t = tab_view<SAT>(smem, a.dt);
+    const TabView<CH> t = tab_view<CH>(smem, a.dt);
     const FlipTerm* flips = (const FlipTerm*)(smem + flip_off);
     const int8_t* dpos = (const int8_t*)(smem + diag_off);
     const W* __restrict__ reps = (const W*)a.reps;
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long n_gather = 0, n_skip = 0, n_miss = 0;
-    const int nvec = a.nvec;
+    const int nvec = NV == 1 ? 1 : a.nvec;
     const int64_t D = a.D;
     for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < D; row += nwarps) {
         const W s = reps[row];
@@ -95,9 +95,9 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
             anti = __reduce_add_sync(0xffffffffu, anti);
             diag += 0.25 * dc.J * (double)(dc.count - 2 * anti);
         }
-        R accr[MAXV], acci[MAXV];
+        R accr[NV], acci[NV];
 #pragma unroll
-        for (int v = 0; v < MAXV; ++v) { accr[v] = 0; acci[v] = 0; }
+        for (int v = 0; v < NV; ++v) { accr[v] = 0; acci[v] = 0; }
         for (int f = lane; f < a.n_flip; f += 32) {
             const FlipTerm ft = flips[f];
             const int ba = (int)((s >> ft.pa) & 1), bb = (int)((s >> ft.pb) & 1);
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
             W r;
             int g, nst;
             bool cp;
-            find_rep<W, SAT>(tau, t, r, g, nst, cp);
+            find_rep<W, CH>(tau, t, r, g, nst, cp);
             if (!cp) { ++n_skip; continue; }
             const int64_t j = find_index<W>(r, reps, dir_base, dir_q, a.limits, a.L);
             if (j < 0) { ++n_miss; continue; }
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
                 if constexpr (K == 0) c = (R)ft.jhalf * t.chi[g].x * t.sqrtn[nst];
                 else c = (R)ft.jhalf * t.chif[g].x * t.sqrtnf[nst];
 #pragma unroll
-                for (int v = 0; v < MAXV; ++v)
+                for (int v = 0; v < NV; ++v)
                     if (v < nvec) accr[v] += c * x[(int64_t)v * D + j];
             } else {
                 // h = jhalf + i * sum_t k_t s^z_c (a down ? +1 : -1)
@@ -139,7 +139,7 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
                     ci = (jh * ch.y - hm * ch.x) * sq;
                 }
 #pragma unroll
-                for (int v = 0; v < MAXV; ++v)
+                for (int v = 0; v < NV; ++v)
                     if (v < nvec) {
                         const T xj = x[(int64_t)v * D + j];
                         accr[v] += cr * xj.x - ci * xj.y;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) hx_kernel(HxArgs a) {
         }
         const int ni = a.stab[row];
 #pragma unroll
-        for (int v = 0; v < MAXV; ++v) {
+        for (int v = 0; v < NV; ++v) {
             if (v < nvec) {
                 const R sr = warp_sum<R>(accr[v]);
                 R si = 0;
@@ -192,35 +192,48 @@ static size_t smem_bytes(const ed_hamiltonian* h) {
 
 size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype) { return smem_bytes(h); }
 
-template <typename W, typename SAT, int K>
+template <typename W, bool CH, int K, int NV>
 static ed_status launch(const HxArgs& a, size_t smem, cudaStream_t s) {
-    auto k = hx_kernel<W, SAT, K>;
-    static int configured_smem = -1;  // per instantiation
-    if ((int)smem > configured_smem) {
+    auto k = hx_kernel<W, CH, K, NV>;
+    // per instantiation: block size with the most resident warps, and the grid
+    static int cfg_smem = -1, cfg_block = 0, cfg_grid = 0;
+    if ((int)smem != cfg_smem) {
         ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        configured_smem = (int)smem;
+        int dev = 0, sms = 0;
+        ED_CUDA(cudaGetDevice(&dev));
+        ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        int best_warps = 0, best_block = 0, best_per_sm = 0;
+        for (int bs : {256, 512, 1024}) {
+            int per_sm = 0;
+            ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, bs, smem));
+            if (per_sm * bs / 32 > best_warps) { best_warps = per_sm * bs / 32; best_block = bs; best_per_sm = per_sm; }
+        }
+        if (best_warps == 0)
+            return fail(ED_ERR_TABLE_TOO_LARGE, "H.x shared memory (%zu bytes) exceeds the device limit", smem);
+        cfg_smem = (int)smem;
+        cfg_block = best_block;
+        cfg_grid = sms * best_per_sm;
     }
-    int dev = 0, sms = 0, per_sm = 0;
-    ED_CUDA(cudaGetDevice(&dev));
-    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
-    if (per_sm < 1) return fail(ED_ERR_TABLE_TOO_LARGE, "H.x shared memory (%zu bytes) exceeds the device limit", smem);
-    const int64_t warps_needed = a.D;
-    int64_t grid = (int64_t)sms * per_sm;
-    grid = std::min<int64_t>(grid, (warps_needed + 7) / 8);
+    const int64_t warps_per_block = cfg_block / 32;
+    int64_t grid = std::min<int64_t>(cfg_grid, (a.D + warps_per_block - 1) / warps_per_block);
     if (grid < 1) grid = 1;
-    k<<<(unsigned)grid, 256, smem, s>>>(a);
+    k<<<(unsigned)grid, cfg_block, smem, s>>>(a);
     ED_CUDA(cudaGetLastError());
     return ED_OK;
 }
 
-template <typename W, typename SAT>
+template <typename W, bool CH, int K>
+static ed_status launch_nv(const HxArgs& a, size_t smem, cudaStream_t s) {
+    return a.nvec == 1 ? launch<W, CH, K, 1>(a, smem, s) : launch<W, CH, K, MAXV>(a, smem, s);
+}
+
+template <typename W, bool CH>
 static ed_status dispatch_k(const HxArgs& a, size_t smem, ed_dtype dt, cudaStream_t s) {
     switch (dt) {
-        case ED_F64: return launch<W, SAT, 0>(a, smem, s);
-        case ED_F32: return launch<W, SAT, 1>(a, smem, s);
-        case ED_C128: return launch<W, SAT, 2>(a, smem, s);
-        case ED_C64: return launch<W, SAT, 3>(a, smem, s);
+        case ED_F64: return launch_nv<W, CH, 0>(a, smem, s);
+        case ED_F32: return launch_nv<W, CH, 1>(a, smem, s);
+        case ED_C128: return launch_nv<W, CH, 2>(a, smem, s);
+        case ED_C64: return launch_nv<W, CH, 3>(a, smem, s);
     }
     return fail(ED_ERR_ARG, "bad dtype");
 }
@@ -250,9 +263,9 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
     a.counters = (unsigned long long*)h->d_counters.p;
     ED_CUDA(cudaMemsetAsync(h->d_counters.p, 0, 24, s));
     const size_t smem = smem_bytes(h);
-    const bool w8 = b->word == 8, s8 = b->dt.sa_bytes == 1;
-    if (w8) return s8 ? dispatch_k<uint64_t, uint8_t>(a, smem, dt, s) : dispatch_k<uint64_t, uint16_t>(a, smem, dt, s);
-    return s8 ? dispatch_k<uint32_t, uint8_t>(a, smem, dt, s) : dispatch_k<uint32_t, uint16_t>(a, smem, dt, s);
+    const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
+    if (w8) return ch ? dispatch_k<uint64_t, true>(a, smem, dt, s) : dispatch_k<uint64_t, false>(a, smem, dt, s);
+    return ch ? dispatch_k<uint32_t, true>(a, smem, dt, s) : dispatch_k<uint32_t, false>(a, smem, dt, s);
 }
 
 }  // namespace ed

@@ -7,7 +7,7 @@
 // so only values with Rep_0(v) = v can start a representative.  Inside a
 // segment the remaining L = N - m bits run over all integers with popcount
 // n_up - popcount(v) in increasing order, so the concatenation of segments in
-// order of v is sorted.  Each thread owns a chunk of CH consecutive
+// order of v is sorted.  Each thread owns a chunk of CANDS consecutive
 // candidates: it unranks the first one (combinatorial number system) and
 // steps with the next-same-popcount rule.  A first pass counts kept states per
 // chunk, an exclusive scan gives output offsets, a second pass writes them.
@@ -23,7 +23,7 @@ namespace ed {
 
 __constant__ uint64_t c_binom[65][65];
 
-static const int CH = 128;  // candidates per thread
+static const int CANDS = 128;  // candidates per thread
 
 struct Seg {
     uint32_t v;         // top-block value
@@ -66,12 +66,12 @@ struct EnumArgs {
     uint16_t* stab;            // pass 1 output
 };
 
-template <typename W, typename SAT, int PASS>
+template <typename W, bool CHK, int PASS>
 __global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     stage_blob(smem, a.dt.blob, a.dt.blob_bytes);
     __syncthreads();
-    const TabView<SAT> t = tab_view<SAT>(smem, a.dt);
+    const TabView<CHK> t = tab_view<CHK>(smem, a.dt);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n_chunks; c += stride) {
         // segment of chunk c
@@ -82,8 +82,8 @@ __global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
             else hi = mid - 1;
         }
         const Seg sg = a.segs[lo];
-        const uint64_t r0 = (c - sg.chunk0) * CH;
-        const uint64_t n = min((uint64_t)CH, sg.size - r0);
+        const uint64_t r0 = (c - sg.chunk0) * CANDS;
+        const uint64_t n = min((uint64_t)CANDS, sg.size - r0);
         W suf = unrank<W>(r0, a.L, sg.k);
         const W top = (W)sg.v << a.L;
         uint32_t kept = 0;
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
             const W s = top | suf;
             int ns;
             bool cp;
-            if (is_rep<W, SAT>(s, t, ns, cp) && cp) {
+            if (is_rep<W, CHK>(s, t, ns, cp) && cp) {
                 if (PASS) {
                     ((W*)a.reps)[out] = s;
                     a.stab[out] = (uint16_t)ns;
@@ -220,11 +220,51 @@ __global__ void limits_kernel(const W* reps, uint64_t D, const uint32_t* seg_bas
     if (blockIdx.x == 0 && threadIdx.x == 0) limits[n_keys] = (uint32_t)D;
 }
 
+// ---------------------------------------------------------------- representatives of given states
+template <typename W, bool CH>
+__global__ void __launch_bounds__(256) rep_kernel(DevTables dt, const uint64_t* states, int64_t n, uint64_t* rep,
+                                                  int32_t* gout, int32_t* nst, uint8_t* cmp) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    stage_blob(smem, dt.blob, dt.blob_bytes);
+    __syncthreads();
+    const TabView<CH> t = tab_view<CH>(smem, dt);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        W r;
+        int g, ns;
+        bool cp;
+        find_rep<W, CH>((W)states[i], t, r, g, ns, cp);
+        rep[i] = (uint64_t)r;
+        gout[i] = g;
+        nst[i] = ns;
+        cmp[i] = cp ? 1 : 0;
+    }
+}
+
+template <typename W, bool CH>
+static ed_status launch_rep(const ed_basis* b, const uint64_t* st, int64_t n, uint64_t* r, int32_t* g, int32_t* ns,
+                            uint8_t* cp, cudaStream_t s) {
+    auto k = rep_kernel<W, CH>;
+    const size_t smem = b->dt.blob_bytes;
+    ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
+    k<<<grid, 256, smem, s>>>(b->dt, st, n, r, g, ns, cp);
+    ED_CUDA(cudaGetLastError());
+    return ED_OK;
+}
+
+ed_status representatives_device(const ed_basis* b, const uint64_t* st, int64_t n, uint64_t* r, int32_t* g, int32_t* ns,
+                                 uint8_t* cp, cudaStream_t s) {
+    const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
+    if (w8) return ch ? launch_rep<uint64_t, true>(b, st, n, r, g, ns, cp, s) : launch_rep<uint64_t, false>(b, st, n, r, g, ns, cp, s);
+    return ch ? launch_rep<uint32_t, true>(b, st, n, r, g, ns, cp, s) : launch_rep<uint32_t, false>(b, st, n, r, g, ns, cp, s);
+}
+
 // ---------------------------------------------------------------- host
-ed_status upload_tables(ed_basis* b, cudaStream_t s) {
-    const HostTables& t = b->ht;
+void make_blob(const HostTables& t, DevTables& d, std::vector<uint8_t>& h) {
     const int S = 1 << t.m;
-    const int sab = t.m <= 8 ? 1 : 2;
+    const bool chunked = t.chunk_lo > 0;
+    const int stride = chunked ? (1 << (t.m - t.chunk_lo)) + (1 << t.chunk_lo) : S;
+    const int eb = chunked ? 2 : 1;
     size_t off = 0;
     auto al = [&](size_t n) {
         off = (off + 15) & ~(size_t)15;
@@ -232,32 +272,33 @@ ed_status upload_tables(ed_basis* b, cudaStream_t s) {
         off += n;
         return (uint32_t)o;
     };
-    DevTables& d = b->dt;
-    d.N = t.N; d.G = t.G; d.n_sub = t.n_sub; d.m = t.m; d.sa_bytes = sab;
+    d.N = t.N; d.G = t.G; d.n_sub = t.n_sub; d.m = t.m; d.sa_bytes = eb;
+    d.chunk_lo = t.chunk_lo;
+    d.lmap_stride = stride;
     d.off_rep = al((size_t)t.n_sub * S * 2);
     d.off_symoff = al((size_t)t.n_sub * (S + 1) * 4);
     d.off_symids = al(std::max<size_t>(t.sym_ids.size(), 1) * 2);
-    d.off_sa = al((size_t)t.G * t.n_sub * S * sab);
-    d.off_src = al((size_t)t.G * t.n_sub);
+    d.off_sa = al((size_t)t.n_lmap * stride * eb);
+    d.off_src = al((size_t)t.G * t.n_sub * 4);
     d.off_chi = al((size_t)t.G * 16);
-    d.off_chione = al((size_t)t.G);
+    d.off_chicls = al((size_t)t.G * 2);
     d.off_sqrt = al((size_t)2 * (t.G + 1) * 8);
     d.off_chif = al((size_t)t.G * 8);
     d.off_sqrtf = al((size_t)2 * (t.G + 1) * 4);
     const size_t total = (off + 15) & ~(size_t)15;
     d.blob_bytes = total;
-    std::vector<uint8_t> h(total, 0);
+    h.assign(total, 0);
     memcpy(&h[d.off_rep], t.rep.data(), t.rep.size() * 2);
     memcpy(&h[d.off_symoff], t.sym_off.data(), t.sym_off.size() * 4);
     if (!t.sym_ids.empty()) memcpy(&h[d.off_symids], t.sym_ids.data(), t.sym_ids.size() * 2);
-    if (sab == 1) {
-        for (size_t i = 0; i < t.sa.size(); ++i) h[d.off_sa + i] = (uint8_t)t.sa[i];
+    if (!chunked) {
+        for (size_t i = 0; i < t.lmap_tab.size(); ++i) h[d.off_sa + i] = (uint8_t)t.lmap_tab[i];
     } else {
-        memcpy(&h[d.off_sa], t.sa.data(), t.sa.size() * 2);
+        memcpy(&h[d.off_sa], t.lmap_tab.data(), t.lmap_tab.size() * 2);
     }
-    memcpy(&h[d.off_src], t.src.data(), t.src.size());
+    memcpy(&h[d.off_src], t.srclid.data(), t.srclid.size() * 4);
     memcpy(&h[d.off_chi], t.chi.data(), (size_t)t.G * 16);
-    memcpy(&h[d.off_chione], t.chi_one.data(), (size_t)t.G);
+    memcpy(&h[d.off_chicls], t.chi_cls.data(), (size_t)t.G * 2);
     std::vector<double> sq(2 * (size_t)(t.G + 1));
     for (int k = 0; k <= t.G; ++k) {
         sq[k] = sqrt((double)k);
@@ -269,6 +310,13 @@ ed_status upload_tables(ed_basis* b, cudaStream_t s) {
     for (size_t i = 0; i < sq.size(); ++i) sqf[i] = (float)sq[i];
     memcpy(&h[d.off_chif], chif.data(), chif.size() * 4);
     memcpy(&h[d.off_sqrtf], sqf.data(), sqf.size() * 4);
+}
+
+ed_status upload_tables(ed_basis* b, cudaStream_t s) {
+    std::vector<uint8_t> h;
+    DevTables& d = b->dt;
+    make_blob(b->ht, d, h);
+    const size_t total = h.size();
     b->tables.bytes = total;
     b->tables.p = b->alloc.get(total, s);
     if (!b->tables.p) return fail(ED_ERR_NOMEM, "table allocation failed");
@@ -278,9 +326,9 @@ ed_status upload_tables(ed_basis* b, cudaStream_t s) {
     return ED_OK;
 }
 
-template <typename W, typename SAT, int PASS>
+template <typename W, bool CHK, int PASS>
 static ed_status launch_enum(const EnumArgs& a, size_t smem, int sms, cudaStream_t s) {
-    auto k = enum_kernel<W, SAT, PASS>;
+    auto k = enum_kernel<W, CHK, PASS>;
     ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem));
@@ -293,18 +341,18 @@ static ed_status launch_enum(const EnumArgs& a, size_t smem, int sms, cudaStream
     return ED_OK;
 }
 
-template <typename W, typename SAT>
+template <typename W, bool CHK>
 static ed_status enum_both(ed_basis* b, EnumArgs& a, size_t smem, int sms, cudaStream_t s, int pass) {
-    return pass == 0 ? launch_enum<W, SAT, 0>(a, smem, sms, s) : launch_enum<W, SAT, 1>(a, smem, sms, s);
+    return pass == 0 ? launch_enum<W, CHK, 0>(a, smem, sms, s) : launch_enum<W, CHK, 1>(a, smem, sms, s);
 }
 
 static ed_status run_enum(ed_basis* b, EnumArgs& a, int pass, int sms, cudaStream_t s) {
     const size_t smem = b->dt.blob_bytes;
-    const bool w8 = b->word == 8, s8 = b->dt.sa_bytes == 1;
-    if (w8) return s8 ? enum_both<uint64_t, uint8_t>(b, a, smem, sms, s, pass)
-                      : enum_both<uint64_t, uint16_t>(b, a, smem, sms, s, pass);
-    return s8 ? enum_both<uint32_t, uint8_t>(b, a, smem, sms, s, pass)
-              : enum_both<uint32_t, uint16_t>(b, a, smem, sms, s, pass);
+    const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
+    if (w8) return ch ? enum_both<uint64_t, true>(b, a, smem, sms, s, pass)
+                      : enum_both<uint64_t, false>(b, a, smem, sms, s, pass);
+    return ch ? enum_both<uint32_t, true>(b, a, smem, sms, s, pass)
+              : enum_both<uint32_t, false>(b, a, smem, sms, s, pass);
 }
 
 namespace {
@@ -352,7 +400,7 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
         for (int i = 0; i < k; ++i) C = C * (uint64_t)(L - i) / (uint64_t)(i + 1);
         Seg sg{(uint32_t)v, k, C, chunks};
         segs.push_back(sg);
-        chunks += (C + CH - 1) / CH;
+        chunks += (C + CANDS - 1) / CANDS;
     }
     if (segs.empty() || chunks == 0) return fail(ED_ERR_EMPTY_SECTOR, "sector has dimension 0");
     Scratch sc{&b->alloc, s, {}};

@@ -6,38 +6,52 @@
 
 #include "ed_internal.h"
 
+// Helpers are __host__ __device__ so the exact device logic can also run on the
+// CPU (table-image self-checks and host-side tests).
+#define ED_HD __host__ __device__ __forceinline__
+
 namespace ed {
 
-// View of the sublattice-coding tables after they were staged (to shared or
-// global memory).  SAT is the element type of SymmetryAction (uint8_t for
-// blocks of <= 8 sites, uint16_t otherwise).
-template <typename SAT>
+template <typename T>
+ED_HD T ld_ro(const T* p) {
+#ifdef __CUDA_ARCH__
+    return __ldg(p);
+#else
+    return *p;
+#endif
+}
+
+// View of the sublattice-coding tables after they were staged into shared
+// memory.  CHUNKED selects the SymmetryAction map format: false = one byte
+// table of 2^m entries per distinct local map (m <= 8); true = two uint16
+// chunk tables (high m-c bits, low c bits) whose images are OR-ed.
+template <bool CHUNKED>
 struct TabView {
-    const uint16_t* rep;
-    const uint32_t* sym_off;
-    const uint16_t* sym_ids;
-    const SAT* sa;
-    const uint8_t* src;
+    const uint16_t* rep;      // [n_sub][S]      Rep_X(s)
+    const uint32_t* sym_off;  // [n_sub][S+1]    Sym_X(s) ranges
+    const uint16_t* sym_ids;  //                 group ids
+    const uint32_t* srclid;   // [G][n_sub]      (src block, local map id) for destination block Z
+    const void* lmap;         // map tables
     const double2* chi;
-    const uint8_t* chi_one;
-    const double* sqrtn;     // sqrtn[k] = sqrt(k), k = 0..G
-    const double* isqrtn;    // 1/sqrt(k)
+    const uint16_t* chi_cls;  // character class id; 0 is the class of the value 1
+    const double* sqrtn;      // sqrtn[k] = sqrt(k), k = 0..G
+    const double* isqrtn;     // 1/sqrt(k)
     const float2* chif;
     const float* sqrtnf;
     const float* isqrtnf;
-    int n_sub, m, G;
+    int n_sub, m, G, c_lo, stride;
 };
 
-template <typename SAT>
-__device__ __forceinline__ TabView<SAT> tab_view(const uint8_t* base, const DevTables& d) {
-    TabView<SAT> v;
+template <bool CHUNKED>
+ED_HD TabView<CHUNKED> tab_view(const uint8_t* base, const DevTables& d) {
+    TabView<CHUNKED> v;
     v.rep = (const uint16_t*)(base + d.off_rep);
     v.sym_off = (const uint32_t*)(base + d.off_symoff);
     v.sym_ids = (const uint16_t*)(base + d.off_symids);
-    v.sa = (const SAT*)(base + d.off_sa);
-    v.src = (const uint8_t*)(base + d.off_src);
+    v.srclid = (const uint32_t*)(base + d.off_src);
+    v.lmap = (const void*)(base + d.off_sa);
     v.chi = (const double2*)(base + d.off_chi);
-    v.chi_one = (const uint8_t*)(base + d.off_chione);
+    v.chi_cls = (const uint16_t*)(base + d.off_chicls);
     v.sqrtn = (const double*)(base + d.off_sqrt);
     v.isqrtn = v.sqrtn + (d.G + 1);
     v.chif = (const float2*)(base + d.off_chif);
@@ -46,10 +60,12 @@ __device__ __forceinline__ TabView<SAT> tab_view(const uint8_t* base, const DevT
     v.n_sub = d.n_sub;
     v.m = d.m;
     v.G = d.G;
+    v.c_lo = d.chunk_lo;
+    v.stride = d.lmap_stride;
     return v;
 }
 
-// Cooperative copy of the table image into shared memory (16-byte chunks).
+// Cooperative copy of a table image into shared memory (16-byte chunks).
 __device__ __forceinline__ void stage_blob(uint8_t* dst, const uint8_t* src, size_t bytes) {
     const uint4* s4 = (const uint4*)src;
     uint4* d4 = (uint4*)dst;
@@ -58,44 +74,57 @@ __device__ __forceinline__ void stage_blob(uint8_t* dst, const uint8_t* src, siz
 }
 
 template <typename W>
-__device__ __forceinline__ uint32_t substate(W s, int X, int n_sub, int m) {
+ED_HD uint32_t substate(W s, int X, int n_sub, int m) {
     return (uint32_t)((s >> ((n_sub - 1 - X) * m)) & (((W)1 << m) - 1));
+}
+
+// SymmetryAction_X(g, s) through the local map `lid` (Eq. symactiondef).
+template <bool CHUNKED>
+ED_HD uint32_t sym_action(const TabView<CHUNKED>& t, uint32_t lid, uint32_t s) {
+    if constexpr (!CHUNKED) {
+        return ((const uint8_t*)t.lmap)[lid * t.stride + s];
+    } else {
+        const uint16_t* tab = (const uint16_t*)t.lmap + lid * t.stride;
+        const int hi_n = t.stride - (1 << t.c_lo);
+        return (uint32_t)tab[s >> t.c_lo] | (uint32_t)tab[hi_n + (s & ((1u << t.c_lo) - 1))];
+    }
 }
 
 // Alg. "Sublattice coding algorithm for finding the representative":
 // MinRep = min_X Rep_X(sigma_X); for every block Y with Rep_Y = MinRep and
 // every g in Sym_Y(sigma_Y), compose g.sigma block by block from the most
-// significant destination block (block Z comes from block src(g,Z) via
-// SymmetryAction) and keep the smallest.  Also returns the number of
-// minimising elements, which equals |Stab(rep)|, and whether chi is 1 on all
-// of them (the representative's projector is non-zero iff chi is trivial on
-// the stabilizer).
-template <typename W, typename SAT>
-__device__ __forceinline__ void find_rep(W s, const TabView<SAT>& t, W& rep, int& gbest, int& nstab, bool& compat) {
+// significant destination block (block Z comes from block src(g,Z) through
+// SymmetryAction) and keep the smallest.
+// Outputs: the representative, one minimising element g_tau, the number of
+// minimising elements (the coset Stab(rep) g_tau, so its size is |Stab(rep)|),
+// and whether the representative belongs to the sector: the projector of
+// the representative is non-zero iff chi is trivial on Stab(rep), i.e. iff chi
+// takes one value on the minimising coset.
+template <typename W, bool CHUNKED>
+ED_HD void find_rep(W s, const TabView<CHUNKED>& t, W& rep, int& gbest, int& nstab, bool& compat) {
     const int n_sub = t.n_sub, m = t.m;
     const int S = 1 << m;
     uint32_t minrep = 0xFFFFFFFFu;
     for (int X = 0; X < n_sub; ++X) {
-        uint32_t r = t.rep[X * S + substate(s, X, n_sub, m)];
+        const uint32_t r = t.rep[X * S + substate(s, X, n_sub, m)];
         minrep = r < minrep ? r : minrep;
     }
     W best = ~(W)0;
     int gb = 0, ns = 0;
     bool cp = true;
+    uint32_t cls = 0;
     for (int Y = 0; Y < n_sub; ++Y) {
         const uint32_t sy = substate(s, Y, n_sub, m);
         if (t.rep[Y * S + sy] != minrep) continue;
         const uint32_t q0 = t.sym_off[Y * (S + 1) + sy], q1 = t.sym_off[Y * (S + 1) + sy + 1];
         for (uint32_t q = q0; q < q1; ++q) {
             const int g = t.sym_ids[q];
-            const uint8_t* srcg = t.src + g * n_sub;
-            const SAT* sag = t.sa + (size_t)g * n_sub * S;
+            const uint32_t* sl = t.srclid + g * n_sub;
             W img = (W)minrep;
-            int Z = 1;
             int cmp = 0;  // sign of (img prefix - best prefix) once decided
-            for (; Z < n_sub; ++Z) {
-                const int X = srcg[Z];
-                img = (img << m) | (W)sag[X * S + substate(s, X, n_sub, m)];
+            for (int Z = 1; Z < n_sub; ++Z) {
+                const uint32_t e = sl[Z];
+                img = (img << m) | (W)sym_action<CHUNKED>(t, e >> 8, substate(s, (int)(e & 0xFFu), n_sub, m));
                 if (cmp == 0) {
                     const W bp = best >> ((n_sub - 1 - Z) * m);
                     if (img > bp) { cmp = 1; break; }
@@ -104,10 +133,10 @@ __device__ __forceinline__ void find_rep(W s, const TabView<SAT>& t, W& rep, int
             }
             if (cmp > 0) continue;
             if (img < best) {
-                best = img; gb = g; ns = 1; cp = t.chi_one[g];
+                best = img; gb = g; ns = 1; cls = t.chi_cls[g]; cp = true;
             } else if (img == best) {
                 ++ns;
-                cp = cp && t.chi_one[g];
+                cp = cp && (t.chi_cls[g] == cls);
             }
         }
     }
@@ -118,15 +147,15 @@ __device__ __forceinline__ void find_rep(W s, const TabView<SAT>& t, W& rep, int
 }
 
 // Is s its own representative?  Early exit as soon as some g.s < s.
-// On success returns |Stab(s)| in nstab and whether chi is trivial on it.
-template <typename W, typename SAT>
-__device__ __forceinline__ bool is_rep(W s, const TabView<SAT>& t, int& nstab, bool& compat) {
+// On success returns |Stab(s)| in nstab and whether chi is 1 on Stab(s).
+template <typename W, bool CHUNKED>
+ED_HD bool is_rep(W s, const TabView<CHUNKED>& t, int& nstab, bool& compat) {
     const int n_sub = t.n_sub, m = t.m;
     const int S = 1 << m;
     const uint32_t top = substate(s, 0, n_sub, m);
     uint32_t minrep = 0xFFFFFFFFu;
     for (int X = 0; X < n_sub; ++X) {
-        uint32_t r = t.rep[X * S + substate(s, X, n_sub, m)];
+        const uint32_t r = t.rep[X * S + substate(s, X, n_sub, m)];
         if (r < top) return false;
         minrep = r < minrep ? r : minrep;
     }
@@ -138,19 +167,18 @@ __device__ __forceinline__ bool is_rep(W s, const TabView<SAT>& t, int& nstab, b
         const uint32_t q0 = t.sym_off[Y * (S + 1) + sy], q1 = t.sym_off[Y * (S + 1) + sy + 1];
         for (uint32_t q = q0; q < q1; ++q) {
             const int g = t.sym_ids[q];
-            const uint8_t* srcg = t.src + g * n_sub;
-            const SAT* sag = t.sa + (size_t)g * n_sub * S;
+            const uint32_t* sl = t.srclid + g * n_sub;
             int cmp = 0;
             for (int Z = 1; Z < n_sub; ++Z) {
-                const int X = srcg[Z];
-                const uint32_t v = sag[X * S + substate(s, X, n_sub, m)];
+                const uint32_t e = sl[Z];
+                const uint32_t v = sym_action<CHUNKED>(t, e >> 8, substate(s, (int)(e & 0xFFu), n_sub, m));
                 const uint32_t sz = substate(s, Z, n_sub, m);
                 if (v < sz) return false;
                 if (v > sz) { cmp = 1; break; }
             }
             if (cmp == 0) {
                 ++ns;
-                cp = cp && t.chi_one[g];
+                cp = cp && (t.chi_cls[g] == 0);
             }
         }
     }
@@ -165,21 +193,21 @@ __device__ __forceinline__ bool is_rep(W s, const TabView<SAT>& t, int& nstab, b
 // the next q_v bits select a bucket [limits[key], limits[key+1]) of the
 // ascending basis.  Returns -1 if r is absent.
 template <typename W>
-__device__ __forceinline__ int64_t find_index(W r, const W* __restrict__ reps, const uint32_t* __restrict__ dir_base,
+ED_HD int64_t find_index(W r, const W* __restrict__ reps, const uint32_t* __restrict__ dir_base,
                                               const uint8_t* __restrict__ dir_q, const uint32_t* __restrict__ limits,
                                               int L) {
     const uint32_t top = (uint32_t)(r >> L);
     const int q = dir_q[top];
     const W low = L ? (r & (((W)1 << L) - 1)) : (W)0;
     const uint32_t key = dir_base[top] + (q ? (uint32_t)(low >> (L - q)) : 0u);
-    uint32_t lo = __ldg(limits + key), hi = __ldg(limits + key + 1);
+    uint32_t lo = ld_ro(limits + key), hi = ld_ro(limits + key + 1);
     const uint32_t end = hi;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;
-        if (__ldg(reps + mid) < r) lo = mid + 1;
+        if (ld_ro(reps + mid) < r) lo = mid + 1;
         else hi = mid;
     }
-    return (lo < end && __ldg(reps + lo) == r) ? (int64_t)lo : -1;
+    return (lo < end && ld_ro(reps + lo) == r) ? (int64_t)lo : -1;
 }
 
 }  // namespace ed

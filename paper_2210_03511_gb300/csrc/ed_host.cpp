@@ -92,16 +92,24 @@ ed_status build_host_tables(const ed_sector* sec, HostTables& t) {
     for (int g = 0; g < G; ++g)
         if (t.flip[g] && 2 * t.n_up != N)
             return fail(ED_ERR_SPINFLIP_SZ, "spin flip needs n_up = N/2 (n_up=%d, N=%d)", t.n_up, N);
-    // characters
-    t.chi_one.assign(G, 0);
+    // characters, grouped into classes of equal value (class 0 = the value 1)
+    t.chi_cls.assign(G, 0);
     t.real_chars = true;
+    {
+        double re0 = t.chi[0], im0 = t.chi[1];
+        if (fabs(re0 - 1.0) > 1e-9 || fabs(im0) > 1e-9) return fail(ED_ERR_CHAR_NOT_HOMOMORPHISM, "chi(identity) != 1");
+    }
+    std::vector<std::pair<double, double>> cls_val;
     for (int g = 0; g < G; ++g) {
         double re = t.chi[2 * g], im = t.chi[2 * g + 1];
         if (fabs(re * re + im * im - 1.0) > 1e-9) return fail(ED_ERR_CHAR_NOT_HOMOMORPHISM, "|chi(%d)| != 1", g);
-        t.chi_one[g] = (fabs(re - 1.0) < 1e-9 && fabs(im) < 1e-9);
         if (fabs(im) > 1e-12) t.real_chars = false;
+        int c = -1;
+        for (size_t k = 0; k < cls_val.size(); ++k)
+            if (fabs(cls_val[k].first - re) < 1e-9 && fabs(cls_val[k].second - im) < 1e-9) { c = (int)k; break; }
+        if (c < 0) { c = (int)cls_val.size(); cls_val.push_back({re, im}); }
+        t.chi_cls[g] = (uint16_t)c;
     }
-    if (!t.chi_one[0]) return fail(ED_ERR_CHAR_NOT_HOMOMORPHISM, "chi(identity) != 1");
     // closure and homomorphism
     std::unordered_map<std::string, int> index;
     index.reserve((size_t)G * 2);
@@ -179,6 +187,50 @@ ed_status build_host_tables(const ed_sector* sec, HostTables& t) {
         }
         t.sym_off[(size_t)X * (S + 1) + S] = (uint32_t)t.sym_ids.size();
     }
+    // distinct local block maps (positions + flip) and their SymmetryAction tables
+    t.chunk_lo = m <= 8 ? 0 : m / 2;
+    const int c_lo = t.chunk_lo, c_hi = m - c_lo;
+    const int stride = m <= 8 ? S : (1 << c_hi) + (1 << c_lo);
+    std::map<std::vector<int>, int> lmap_id;
+    t.srclid.assign((size_t)G * n_sub, 0);
+    t.lmap_tab.clear();
+    for (int g = 0; g < G; ++g)
+        for (int X = 0; X < n_sub; ++X) {
+            const int Z = t.dest[(size_t)g * n_sub + X];
+            std::vector<int> key(m + 1);
+            for (int l = 0; l < m; ++l) key[l] = t.perm[(size_t)g * N + X * m + l] - Z * m;
+            key[m] = t.flip[g];
+            auto it = lmap_id.find(key);
+            int id;
+            if (it == lmap_id.end()) {
+                id = (int)lmap_id.size();
+                lmap_id[key] = id;
+                // image of a set of local bits (complemented first for a flip element)
+                auto img = [&](uint32_t bits, uint32_t within) {
+                    uint32_t out = 0;
+                    for (int l = 0; l < m; ++l) {
+                        if (!((within >> (m - 1 - l)) & 1)) continue;
+                        int bit = (bits >> (m - 1 - l)) & 1;
+                        if (key[m]) bit ^= 1;
+                        if (bit) out |= 1u << (m - 1 - key[l]);
+                    }
+                    return (uint16_t)out;
+                };
+                const uint32_t full = (1u << m) - 1;
+                if (m <= 8) {
+                    for (int s2 = 0; s2 < S; ++s2) t.lmap_tab.push_back(img((uint32_t)s2, full));
+                } else {
+                    const uint32_t hi_mask = full & ~((1u << c_lo) - 1), lo_mask = (1u << c_lo) - 1;
+                    for (int h = 0; h < (1 << c_hi); ++h) t.lmap_tab.push_back(img((uint32_t)h << c_lo, hi_mask));
+                    for (int l2 = 0; l2 < (1 << c_lo); ++l2) t.lmap_tab.push_back(img((uint32_t)l2, lo_mask));
+                }
+            } else {
+                id = it->second;
+            }
+            t.srclid[(size_t)g * n_sub + Z] = (uint32_t)X | ((uint32_t)id << 8);
+        }
+    t.n_lmap = (int)lmap_id.size();
+    (void)stride;
     return ED_OK;
 }
 
@@ -374,6 +426,43 @@ ed_status ed_sector_tables(const ed_sector* sector, uint16_t* rep, uint32_t* sym
     if (sa) memcpy(sa, t.sa.data(), t.sa.size() * 2);
     if (dest) memcpy(dest, t.dest.data(), t.dest.size());
     return ED_OK;
+}
+
+ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
+                             int32_t* nstab, uint8_t* compat) {
+    if (!sector || (n > 0 && !states) || n < 0) return fail(ED_ERR_ARG, "bad arguments");
+    ed_basis tmp;
+    ed_status st = build_host_tables(sector, tmp.ht);
+    if (st != ED_OK || n == 0) return st;
+    ED_CUDA(cudaGetDevice(&tmp.device));
+    tmp.word = tmp.ht.N <= 32 ? 4 : 8;
+    st = upload_tables(&tmp, 0);
+    if (st != ED_OK) return st;
+    const size_t per = 8 + 8 + 4 + 4 + 1;
+    uint8_t* d = (uint8_t*)tmp.alloc.get((size_t)n * per + 64, 0);
+    if (!d) {
+        tmp.alloc.put(tmp.tables.p, tmp.tables.bytes, 0);
+        return fail(ED_ERR_NOMEM, "scratch for %lld states", (long long)n);
+    }
+    uint64_t* ds = (uint64_t*)d;
+    uint64_t* dr = ds + n;
+    int32_t* dg = (int32_t*)(dr + n);
+    int32_t* dn = dg + n;
+    uint8_t* dc = (uint8_t*)(dn + n);
+    const uint64_t mask = tmp.ht.N == 64 ? ~0ull : ((1ull << tmp.ht.N) - 1);
+    std::vector<uint64_t> clean(states, states + n);
+    for (auto& v : clean) v &= mask;
+    if (cudaMemcpy(ds, clean.data(), (size_t)n * 8, cudaMemcpyHostToDevice) != cudaSuccess) st = fail(ED_ERR_CUDA, "copy");
+    if (st == ED_OK) st = representatives_device(&tmp, ds, n, dr, dg, dn, dc, 0);
+    if (st == ED_OK && cudaDeviceSynchronize() != cudaSuccess) st = fail(ED_ERR_CUDA, "representative kernel failed");
+    if (st == ED_OK && rep) cudaMemcpy(rep, dr, (size_t)n * 8, cudaMemcpyDeviceToHost);
+    if (st == ED_OK && g) cudaMemcpy(g, dg, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    if (st == ED_OK && nstab) cudaMemcpy(nstab, dn, (size_t)n * 4, cudaMemcpyDeviceToHost);
+    if (st == ED_OK && compat) cudaMemcpy(compat, dc, (size_t)n, cudaMemcpyDeviceToHost);
+    tmp.alloc.put(d, (size_t)n * per + 64, 0);
+    tmp.alloc.put(tmp.tables.p, tmp.tables.bytes, 0);
+    tmp.tables.p = nullptr;
+    return st;
 }
 
 void ed_basis_free(ed_basis* b) {

@@ -52,8 +52,17 @@ struct HostTables {
     std::vector<uint32_t> sym_off;  // [n_sub][S+1]
     std::vector<uint16_t> sym_ids;
     std::vector<uint16_t> sa;       // [G][n_sub][S]
-    std::vector<uint8_t> chi_one;   // [G] chi(g) == 1
+    std::vector<uint16_t> chi_cls;  // [G] id of the value chi(g); equal ids <=> equal characters
     bool real_chars = true;
+    // SymmetryAction stored once per distinct local block map (a permutation of
+    // the m positions of a block plus the flip bit): srclid[g*n_sub + Z] packs
+    // the source block X = src(g, Z) (low 8 bits) and the map id (high bits).
+    // For m <= 8 a map is one table of S bytes; for m > 8 it is two chunk
+    // tables (high m - c and low c = m/2 bits) of uint16 images that are OR-ed.
+    int n_lmap = 0;
+    std::vector<uint32_t> srclid;   // [G][n_sub]
+    std::vector<uint16_t> lmap_tab; // [n_lmap][table entries per map]
+    int chunk_lo = 0;               // c (0 when m <= 8)
 };
 
 ed_status build_host_tables(const ed_sector* sec, HostTables& t);
@@ -65,8 +74,10 @@ struct DevTables {
     const uint8_t* blob;     // contiguous device image (see tables_blob layout)
     size_t blob_bytes;
     // offsets (bytes) inside the blob
-    uint32_t off_rep, off_symoff, off_symids, off_sa, off_src, off_chi, off_chione, off_sqrt;
+    uint32_t off_rep, off_symoff, off_symids, off_sa, off_src, off_chi, off_chicls, off_sqrt;
     uint32_t off_chif, off_sqrtf;   // float copies of chi and sqrt tables for FP32 vectors
+    int chunk_lo;                   // low chunk bits of SymmetryAction maps (0: single table)
+    int lmap_stride;                // entries per map
 };
 
 // ---------------------------------------------------------------- flip terms (host + device)
@@ -128,6 +139,9 @@ namespace ed {
 // implemented in ed_basis.cu
 ed_status basis_build_device(ed_basis* b, cudaStream_t s);
 ed_status upload_tables(ed_basis* b, cudaStream_t s);
+void make_blob(const HostTables& t, DevTables& d, std::vector<uint8_t>& image);
+ed_status representatives_device(const ed_basis* b, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
+                                 int32_t* nstab, uint8_t* compat, cudaStream_t s);
 // implemented in ed_apply.cu
 ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
 size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype dt);

@@ -309,7 +309,7 @@ static int dtype_kind(ed_dtype d) { return d == ED_F64 ? 0 : d == ED_F32 ? 1 : d
 
 template <int K>
 static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
-                     ed_lanczos_report* rep, cudaStream_t s) {
+                     ed_lanczos_report* rep, cudaStream_t s, const void* start = nullptr) {
     using T = typename LV<K>::T;
     auto t0 = std::chrono::steady_clock::now();
     Lz<K> z;
@@ -336,8 +336,9 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         multi_dot<K><<<dim3(z.nb, nk), 256, 0, s>>>(A, D, bv, D, partial);
         reduce_partials<<<std::min(nk, 1024), 256, 0, s>>>(partial, z.nb, nk, out);
     };
-    // v_1: keyed random, normalised
-    if (h->basis->word == 8) init_random<uint64_t, K><<<g, 256, 0, s>>>(vec(0), (const uint64_t*)h->basis->reps.p, D, o->seed);
+    // v_1: keyed random (or the caller's start vector), normalised
+    if (start) ED_CUDA(cudaMemcpyAsync(vec(0), start, (size_t)D * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    else if (h->basis->word == 8) init_random<uint64_t, K><<<g, 256, 0, s>>>(vec(0), (const uint64_t*)h->basis->reps.p, D, o->seed);
     else init_random<uint32_t, K><<<g, 256, 0, s>>>(vec(0), (const uint32_t*)h->basis->reps.p, D, o->seed);
     dot(vec(0), 1, vec(0), coef);
     sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
@@ -349,6 +350,9 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     int n_apply = 0, iters = 0;
     bool conv = false;
     const int every = std::max(1, o->check_every);
+    // FP32 vectors resolve eigenvalues to ~1e-7 relative: their phase runs at
+    // a tolerance of at least 1e-6 and `tol` is the target of the refinement.
+    const double tol = (K == 1 || K == 3) ? std::max(o->tol, 1e-6) : o->tol;
     ed_dtype vdt = o->dtype;
     for (int n = 0; n < max_it; ++n) {
         ed_status st = apply_launch(h, vdt, vec(n), w, 1, s);
@@ -377,26 +381,30 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         const bool breakdown = bh < 1e-13 * tnorm;
         const bool last = breakdown || n + 1 == max_it;
         if ((n + 1) % every == 0 || last) {
-            tri_eig(al, be, iters, n_eig, lam, svec);
-            bool ok = (int)lam.size() == n_eig || breakdown;
-            for (int k = 0; k < (int)lam.size() && ok; ++k) {
+            tri_eig(al, be, iters, n_eig + 1, lam, svec);
+            // converged: for each wanted Ritz value, a small change since the
+            // last check and a small residual bound r = beta |s_last| (the
+            // eigenvalue error is at most min(r, r^2/gap)); with eigenvectors
+            // requested also r <= sqrt(tol).  At least n_eig + 3 steps.
+            bool ok = (int)lam.size() >= n_eig && iters >= n_eig + 3;
+            for (int k = 0; k < n_eig && k < (int)lam.size() && ok; ++k) {
                 const double sc = std::max(1.0, fabs(lam[k]));
                 const double rb = bh * fabs(svec[k][iters - 1]);
                 double gap = 1e300;
                 for (int p = 0; p < (int)lam.size(); ++p)
                     if (p != k) gap = std::min(gap, fabs(lam[p] - lam[k]));
-                if (n_eig == 1 && iters > 1) {
-                    std::vector<double> l2;
-                    std::vector<std::vector<double>> s2;
-                    tri_eig(al, be, iters, 2, l2, s2);
-                    if (l2.size() > 1) gap = l2[1] - l2[0];
-                }
-                const bool steady = fabs(lam[k] - prev[k]) <= o->tol * sc;
-                const bool small_res = rb * rb / std::max(gap, 1e-12) <= o->tol * sc || rb <= o->tol * sc;
-                if (!(steady && small_res) && !breakdown) ok = false;
+                const bool steady = fabs(lam[k] - prev[k]) <= 0.1 * tol * sc;
+                const bool small_res = rb <= tol * sc || rb * rb <= tol * sc * gap;
+                const bool vec_ok = !evecs || rb <= sqrt(tol) * sc;
+                if (!(steady && small_res && vec_ok)) ok = false;
             }
-            for (int k = 0; k < (int)lam.size(); ++k) prev[k] = lam[k];
+            if (breakdown) ok = true;
+            for (int k = 0; k < n_eig && k < (int)lam.size(); ++k) prev[k] = lam[k];
             if (ok) conv = true;
+            if ((int)lam.size() > n_eig) {
+                lam.resize(n_eig);
+                svec.resize(n_eig);
+            }
         }
         if (conv || last) break;
         scale_by<K><<<g, 256, 0, s>>>(vec(n + 1), w, D, beta_d);
@@ -414,44 +422,52 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     }
     // Ritz vectors (need stored Lanczos vectors)
     const bool mixed = (K == 1 || K == 3);
-    if (o->reorth && (evecs || (mixed && o->refine))) {
+    if (o->reorth && evecs) {
         double* sd = (double*)z.get((size_t)iters * sizeof(double));
         if (!sd) return fail(ED_ERR_NOMEM, "Ritz workspace");
-        const int K64 = LV<K>::cplx ? 2 : 0;
-        using T64 = typename LV<(LV<K>::cplx ? 2 : 0)>::T;
-        T64* y64 = (mixed && o->refine) ? (T64*)z.get((size_t)D * sizeof(T64)) : nullptr;
-        T64* hy64 = (mixed && o->refine) ? (T64*)z.get((size_t)D * sizeof(T64)) : nullptr;
-        double2* d2 = (double2*)z.get(2 * sizeof(double2));
-        if (mixed && o->refine && (!y64 || !hy64 || !d2)) return fail(ED_ERR_NOMEM, "refinement workspace");
         for (int k = 0; k < nk; ++k) {
             ED_CUDA(cudaMemcpyAsync(sd, svec[k].data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
-            if (evecs) combine<K, T><<<g, 256, 0, s>>>((T*)evecs + (int64_t)k * D, V, D, iters, sd, D);
-            if (mixed && o->refine) {
-                combine<K, T64><<<g, 256, 0, s>>>(y64, V, D, iters, sd, D);
-                ed_status st = apply_launch(h, K64 == 2 ? ED_C128 : ED_F64, y64, hy64, 1, s);
-                if (st != ED_OK) return st;
-                ++n_apply;
-                // E = <y|Hy>/<y|y>, residual ||Hy - E y|| / ||y||
-                multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(y64, D, hy64, D, partial);
-                reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, d2);
-                multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(y64, D, y64, D, partial);
-                reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, d2 + 1);
-                double2 hh[2];
-                ED_CUDA(cudaMemcpyAsync(hh, d2, sizeof hh, cudaMemcpyDeviceToHost, s));
-                ED_CUDA(cudaStreamSynchronize(s));
-                const double E = hh[0].x / hh[1].x;
-                residual<K64><<<g, 256, 0, s>>>(hy64, hy64, y64, D, E);
-                multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(hy64, D, hy64, D, partial);
-                reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, d2);
-                ED_CUDA(cudaMemcpyAsync(hh, d2, sizeof(double2), cudaMemcpyDeviceToHost, s));
-                ED_CUDA(cudaStreamSynchronize(s));
-                r.refined[k] = E;
-                r.refined_resid[k] = sqrt(hh[0].x / hh[1].x);
-                evals[k] = E;
-            }
+            combine<K, T><<<g, 256, 0, s>>>((T*)evecs + (int64_t)k * D, V, D, iters, sd, D);
+            ED_CUDA(cudaStreamSynchronize(s));
         }
-        ED_CUDA(cudaGetLastError());
     }
+    // Mixed precision: FP64 Lanczos polish started from the sum of the FP32
+    // Ritz vectors promoted to FP64 (the Krylov space of a start vector that
+    // already overlaps the wanted eigenvectors converges in a few steps).
+    if constexpr (K == 1 || K == 3) {
+        if (o->reorth && o->refine > 0 && nk > 0) {
+            constexpr int K64 = LV<K>::cplx ? 2 : 0;
+            using T64 = typename LV<K64>::T;
+            double* sd = (double*)z.get((size_t)iters * sizeof(double));
+            T64* y64 = (T64*)z.get((size_t)D * sizeof(T64));
+            if (!sd || !y64) return fail(ED_ERR_NOMEM, "refinement workspace");
+            std::vector<double> ssum(iters, 0.0);
+            for (int k = 0; k < nk; ++k)
+                for (int i = 0; i < iters; ++i) ssum[i] += svec[k][i];
+            ED_CUDA(cudaMemcpyAsync(sd, ssum.data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
+            combine<K, T64><<<g, 256, 0, s>>>(y64, V, D, iters, sd, D);
+            ED_CUDA(cudaStreamSynchronize(s));
+            ed_lanczos_opts o2 = *o;
+            o2.dtype = K64 == 2 ? ED_C128 : ED_F64;
+            o2.max_iter = std::max(o->refine, o->n_eig + 2);
+            o2.refine = 0;
+            o2.check_every = 1;
+            double ev2[8];
+            ed_lanczos_report r2{};
+            ed_status st2 = run<K64>(h, &o2, ev2, nullptr, &r2, s, y64);
+            if (st2 != ED_OK && st2 != ED_ERR_NOT_CONVERGED) return st2;
+            n_apply += r2.n_apply;
+            const int n2 = std::min(nk, o->n_eig);
+            for (int k = 0; k < n2; ++k) {
+                r.refined[k] = r2.ritz[k];
+                r.refined_resid[k] = r2.resid_bound[k];
+                evals[k] = r2.ritz[k];
+            }
+            conv = conv && (r2.converged != 0);
+            if (!r2.converged) conv = false;
+        }
+    }
+    (void)mixed;
     ED_CUDA(cudaStreamSynchronize(s));
     r.n_apply = n_apply;
     r.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

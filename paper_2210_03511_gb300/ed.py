@@ -76,6 +76,8 @@ def lib():
         L.ed_basis_dim.argtypes = [c_vp, P(c_i64)]
         L.ed_basis_export.argtypes = [c_vp, P(c_u64), P(c_u16)]
         L.ed_sector_tables.argtypes = [P(ed_sector), P(c_u16), P(c_u32), P(c_u16), P(c_i64), P(c_u16), P(c_u8)]
+        L.ed_representatives.argtypes = [P(ed_sector), P(c_u64), c_i64, P(c_u64), P(c_i32), P(c_i32), P(c_u8)]
+        L.ed_representatives.restype = ctypes.c_int
         L.ed_basis_free.argtypes = [c_vp]
         L.ed_basis_free.restype = None
         L.ed_hamiltonian_create.argtypes = [c_vp, P(ed_terms), P(c_vp)]
@@ -136,6 +138,20 @@ def sector_tables(sector) -> dict:
                                  ctypes.byref(n), _ptr(sa, c_u16), _ptr(dest, c_u8)))
     return dict(m=m, rep=rep.reshape(n_sub, S), sym_off=off.reshape(n_sub, S + 1), sym_ids=ids[:n.value],
                 sa=sa.reshape(G, n_sub, S), dest=dest.reshape(G, n_sub))
+
+
+def representatives(sector, states):
+    """ed_representatives: (rep, g, |Stab rep|, compatible) of each state, computed on the device."""
+    sec, keep = _sector_struct(sector)
+    st = np.ascontiguousarray(states, dtype=np.uint64)
+    n = len(st)
+    rep = np.zeros(n, np.uint64)
+    g = np.zeros(n, np.int32)
+    ns = np.zeros(n, np.int32)
+    cp = np.zeros(n, np.uint8)
+    check(lib().ed_representatives(ctypes.byref(sec), _ptr(st, c_u64), n, _ptr(rep, c_u64), _ptr(g, c_i32),
+                                   _ptr(ns, c_i32), _ptr(cp, c_u8)))
+    return rep, g, ns, cp.astype(bool)
 
 
 class Basis:
@@ -216,7 +232,8 @@ class Hamiltonian:
                 check_every=1, evecs=None, stream=None, raise_on_nonconv=True):
         if dtype is None:
             dtype = ED_F64 if self.is_real else ED_C128
-        o = ed_lanczos_opts(dtype, n_eig, tol, max_iter, int(reorth), seed, int(refine), check_every)
+        refine = 40 if refine is True else int(refine)
+        o = ed_lanczos_opts(dtype, n_eig, tol, max_iter, int(reorth), seed, refine, check_every)
         ev = (c_dbl * 8)()
         rep = ed_lanczos_report()
         ptr = evecs.data_ptr() if evecs is not None else None

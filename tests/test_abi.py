@@ -148,9 +148,18 @@ def test_validation_errors(P):
 
 
 def test_workload_tables_fit_shared_memory(P):
-    """SymmetryAction for the workloads stays below 96 KB (shared-memory staging)."""
+    """The shared-memory image of the tables stays below 200 KB for every workload: Rep and Sym
+    tables plus SymmetryAction stored once per distinct local block map."""
     for make in (C.square32, C.kagome36, C.triangular24, C.square40):
         s = make().sector
         t = P.sector_tables(s)
-        bytes_sa = s.n_sym * s.n_sublat * (1 << t["m"]) * (1 if t["m"] <= 8 else 2)
-        assert bytes_sa <= 96 * 1024
+        m, n_sub, G = t["m"], s.n_sublat, s.n_sym
+        maps = set()
+        for g in range(G):
+            for X in range(n_sub):
+                Z = int(t["dest"][g, X])
+                maps.add((tuple(int(s.perm[g][X * m + l]) - Z * m for l in range(m)), int(s.spinflip[g])))
+        per_map = (1 << m) if m <= 8 else 2 * ((1 << (m - m // 2)) + (1 << (m // 2)))
+        total = (len(maps) * per_map + t["rep"].size * 2 + t["sym_off"].size * 4 + len(t["sym_ids"]) * 2
+                 + G * n_sub * 4 + G * 40)
+        assert total <= 200 * 1024, (make.__name__, total)
