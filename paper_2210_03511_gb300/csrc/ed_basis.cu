@@ -285,6 +285,9 @@ void make_blob(const HostTables& t, DevTables& d, std::vector<uint8_t>& h) {
     d.off_sqrt = al((size_t)2 * (t.G + 1) * 8);
     d.off_chif = al((size_t)t.G * 8);
     d.off_sqrtf = al((size_t)2 * (t.G + 1) * 4);
+    d.dl_stride = t.dl_stride;
+    d.off_dl = al(std::max<size_t>(t.dl.size(), 1) * 2);
+    d.off_chineg = al((size_t)t.G);
     const size_t total = (off + 15) & ~(size_t)15;
     d.blob_bytes = total;
     h.assign(total, 0);
@@ -310,6 +313,8 @@ void make_blob(const HostTables& t, DevTables& d, std::vector<uint8_t>& h) {
     for (size_t i = 0; i < sq.size(); ++i) sqf[i] = (float)sq[i];
     memcpy(&h[d.off_chif], chif.data(), chif.size() * 4);
     memcpy(&h[d.off_sqrtf], sqf.data(), sqf.size() * 4);
+    if (!t.dl.empty()) memcpy(&h[d.off_dl], t.dl.data(), t.dl.size() * 2);
+    memcpy(&h[d.off_chineg], t.chi_neg.data(), (size_t)t.G);
 }
 
 ed_status upload_tables(ed_basis* b, cudaStream_t s) {

@@ -39,7 +39,9 @@ struct TabView {
     const float2* chif;
     const float* sqrtnf;
     const float* isqrtnf;
-    int n_sub, m, G, c_lo, stride;
+    const uint16_t* dl;       // [G][dl_stride] (dest block << 12) | map id, by source block
+    const uint8_t* chi_neg;   // [G] real chi(g) < 0
+    int n_sub, m, G, c_lo, stride, dl_stride;
 };
 
 template <bool CHUNKED>
@@ -62,6 +64,9 @@ ED_HD TabView<CHUNKED> tab_view(const uint8_t* base, const DevTables& d) {
     v.G = d.G;
     v.c_lo = d.chunk_lo;
     v.stride = d.lmap_stride;
+    v.dl = (const uint16_t*)(base + d.off_dl);
+    v.chi_neg = (const uint8_t*)(base + d.off_chineg);
+    v.dl_stride = d.dl_stride;
     return v;
 }
 
@@ -132,6 +137,57 @@ ED_HD void find_rep(W s, const TabView<CHUNKED>& t, W& rep, int& gbest, int& nst
                 }
             }
             if (cmp > 0) continue;
+            if (img < best) {
+                best = img; gb = g; ns = 1; cls = t.chi_cls[g]; cp = true;
+            } else if (img == best) {
+                ++ns;
+                cp = cp && (t.chi_cls[g] == cls);
+            }
+        }
+    }
+    rep = best;
+    gbest = gb;
+    nstab = ns;
+    compat = cp;
+}
+
+// find_rep for a compile-time number of blocks NS (2..4): substates and
+// block representatives live in registers; every candidate g composes its
+// full image from its source blocks in one pass (one 8-byte load of the packed
+// (dest block, map id) entries, NS map lookups), so candidates cost the same
+// and lanes stay converged.  Same outputs as find_rep.
+template <typename W, bool CHUNKED, int NS>
+ED_HD void find_rep_ns(W s, const TabView<CHUNKED>& t, W& rep, int& gbest, int& nstab, bool& compat) {
+    static_assert(NS >= 2 && NS <= 4, "specialised for 2..4 blocks");
+    const int m = t.m;
+    const int S = 1 << m;
+    uint32_t sub[NS], r[NS];
+    uint32_t minrep = 0xFFFFFFFFu;
+#pragma unroll
+    for (int X = 0; X < NS; ++X) {
+        sub[X] = substate(s, X, NS, m);
+        r[X] = t.rep[X * S + sub[X]];
+        minrep = r[X] < minrep ? r[X] : minrep;
+    }
+    W best = ~(W)0;
+    int gb = 0, ns = 0;
+    bool cp = true;
+    uint32_t cls = 0;
+#pragma unroll
+    for (int Y = 0; Y < NS; ++Y) {
+        if (r[Y] != minrep) continue;
+        const uint32_t q0 = t.sym_off[Y * (S + 1) + sub[Y]], q1 = t.sym_off[Y * (S + 1) + sub[Y] + 1];
+        for (uint32_t q = q0; q < q1; ++q) {
+            const int g = t.sym_ids[q];
+            const uint2 pk = *(const uint2*)(t.dl + (size_t)g * 4);
+            const uint32_t ent[4] = {pk.x & 0xFFFFu, pk.x >> 16, pk.y & 0xFFFFu, pk.y >> 16};
+            W img = 0;
+#pragma unroll
+            for (int X = 0; X < NS; ++X) {
+                const uint32_t Z = ent[X] >> 12;
+                const uint32_t v = sym_action<CHUNKED>(t, ent[X] & 0xFFFu, sub[X]);
+                img |= (W)v << (m * (NS - 1 - (int)Z));
+            }
             if (img < best) {
                 best = img; gb = g; ns = 1; cls = t.chi_cls[g]; cp = true;
             } else if (img == best) {

@@ -231,6 +231,20 @@ ed_status build_host_tables(const ed_sector* sec, HostTables& t) {
         }
     t.n_lmap = (int)lmap_id.size();
     (void)stride;
+    t.dl.clear();
+    t.dl_stride = 0;
+    if (t.n_lmap < 4096 && n_sub <= 16) {
+        t.dl_stride = (n_sub + 3) & ~3;
+        t.dl.assign((size_t)G * t.dl_stride, 0);
+        for (int g = 0; g < G; ++g)
+            for (int Z = 0; Z < n_sub; ++Z) {
+                const uint32_t e = t.srclid[(size_t)g * n_sub + Z];
+                const int X = (int)(e & 0xFFu), lid = (int)(e >> 8);
+                t.dl[(size_t)g * t.dl_stride + X] = (uint16_t)((Z << 12) | lid);
+            }
+    }
+    t.chi_neg.assign(G, 0);
+    for (int g = 0; g < G; ++g) t.chi_neg[g] = t.chi[2 * g] < 0.0 ? 1 : 0;
     return ED_OK;
 }
 
@@ -360,6 +374,21 @@ static ed_status prepare_terms(const ed_basis* b, const ed_terms* tm, ed_hamilto
     }
     h->n_flip = (int)h->flips.size();
     h->is_real = t.real_chars && !cplx_terms;
+    // coefficient classes by exchange amplitude
+    std::vector<double> vals;
+    h->jcls.assign(h->n_flip, 0);
+    for (int f = 0; f < h->n_flip; ++f) {
+        int c = -1;
+        for (size_t k = 0; k < vals.size(); ++k)
+            if (vals[k] == h->flips[f].jhalf) { c = (int)k; break; }
+        if (c < 0) { c = (int)vals.size(); vals.push_back(h->flips[f].jhalf); }
+        if (c > 255) return fail(ED_ERR_ARG, "more than 256 distinct couplings");
+        h->jcls[f] = (uint8_t)c;
+    }
+    h->n_jc = (int)vals.size();
+    h->jhs.assign((size_t)h->n_jc * (t.G + 1), 0.0);
+    for (int c = 0; c < h->n_jc; ++c)
+        for (int n = 0; n <= t.G; ++n) h->jhs[(size_t)c * (t.G + 1) + n] = vals[c] * sqrt((double)n);
     return ED_OK;
 }
 
@@ -492,7 +521,9 @@ ed_status ed_hamiltonian_create(const ed_basis* basis, const ed_terms* terms, ed
     };
     bool ok = up(h->d_flips, h->flips.data(), h->flips.size() * sizeof(FlipTerm)) &&
               up(h->d_diag_pos, h->diag_pos.data(), h->diag_pos.size()) &&
-              up(h->d_diag_cls, h->diag_cls.data(), h->diag_cls.size() * sizeof(DiagClass));
+              up(h->d_diag_cls, h->diag_cls.data(), h->diag_cls.size() * sizeof(DiagClass)) &&
+              up(h->d_jhs, h->jhs.data(), h->jhs.size() * sizeof(double)) &&
+              up(h->d_jcls, h->jcls.data(), h->jcls.size());
     if (ok) {
         h->d_counters.bytes = 32;
         h->d_counters.p = A.get(32, 0);
@@ -519,6 +550,8 @@ void ed_hamiltonian_free(ed_hamiltonian* h) {
     A.put(h->d_diag_pos.p, h->d_diag_pos.bytes, 0);
     A.put(h->d_diag_cls.p, h->d_diag_cls.bytes, 0);
     A.put(h->d_counters.p, h->d_counters.bytes, 0);
+    A.put(h->d_jhs.p, h->d_jhs.bytes, 0);
+    A.put(h->d_jcls.p, h->d_jcls.bytes, 0);
     delete h;
 }
 

@@ -61,6 +61,12 @@ struct HostTables {
     // tables (high m - c and low c = m/2 bits) of uint16 images that are OR-ed.
     int n_lmap = 0;
     std::vector<uint32_t> srclid;   // [G][n_sub]
+    // Per element and SOURCE block X: (dest block Z << 12) | map id, padded to
+    // dl_stride (a multiple of 4) entries per element; empty when a map id does
+    // not fit 12 bits or there are more than 16 blocks.
+    std::vector<uint16_t> dl;
+    int dl_stride = 0;
+    std::vector<uint8_t> chi_neg;   // [G] real chi(g) < 0
     std::vector<uint16_t> lmap_tab; // [n_lmap][table entries per map]
     int chunk_lo = 0;               // c (0 when m <= 8)
 };
@@ -78,6 +84,8 @@ struct DevTables {
     uint32_t off_chif, off_sqrtf;   // float copies of chi and sqrt tables for FP32 vectors
     int chunk_lo;                   // low chunk bits of SymmetryAction maps (0: single table)
     int lmap_stride;                // entries per map
+    uint32_t off_dl, off_chineg;
+    int dl_stride;
 };
 
 // ---------------------------------------------------------------- flip terms (host + device)
@@ -133,6 +141,11 @@ struct ed_hamiltonian {
     std::vector<ed::DiagClass> diag_cls;
     ed::DevBuf d_flips, d_diag_pos, d_diag_cls, d_counters;
     int n_diag_cls = 0;
+    // real coefficients: jhs[c][n] = jhalf_c * sqrt(n) for the distinct jhalf values c
+    int n_jc = 0;
+    std::vector<double> jhs;
+    std::vector<uint8_t> jcls;          // [n_flip]
+    ed::DevBuf d_jhs, d_jcls;
 };
 
 namespace ed {
