@@ -153,6 +153,31 @@ ed_status ed_sector_tables(const ed_sector* sector, uint16_t* rep, uint32_t* sym
 ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
                              int32_t* nstab, uint8_t* compat);
 
+/* ed_representatives_noalloc -- the computation of ed_representatives for
+ * callers that cannot allocate device memory.  Such callers include
+ * applications whose device memory belongs to another runtime's pool (a
+ * framework that reserves the GPU at start-up) and loops that must not call
+ * cudaMalloc/cudaFree because those calls can synchronise the device.  This
+ * entry point calls neither, nor any allocating library routine: the sector's
+ * lookup-table image is copied into a file-scope device array of 224 KB
+ * (229,376 bytes) that every GPU loading the library holds until exit, and
+ * all other memory is the caller's.  (The thesis has no counterpart; this is
+ * a deployment variant.)
+ *   states: DEVICE uint64[n], n_sites-bit states (higher bits must be 0).
+ *   rep, g, nstab, compat: DEVICE outputs [n], written in full; as in
+ *   ed_representatives.  Inputs and outputs are owned by the caller.
+ * Asynchronous on `stream`; the table upload is ordered on the same stream.
+ * The first call on a device looks up the array's device address (with that
+ * device current); make that first call before any stream capture.  Every
+ * call shares the one array, which keeps the last call's table image: calls
+ * that overlap on the GPU (e.g. on different streams) race and must be
+ * serialised by the caller.  Nothing needs zeroing: each call rewrites every
+ * byte of the array that its kernel reads.  Returns ED_ERR_TABLE_TOO_LARGE
+ * if the table image exceeds 224 KB, and the validation errors of
+ * ed_basis_build. */
+ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep,
+                                     int32_t* g, int32_t* nstab, uint8_t* compat, ed_stream stream);
+
 void ed_basis_free(ed_basis* basis);
 
 /* ed_hamiltonian_create -- bind terms to a basis.

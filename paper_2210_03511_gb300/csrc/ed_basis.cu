@@ -259,6 +259,60 @@ ed_status representatives_device(const ed_basis* b, const uint64_t* st, int64_t 
     return ch ? launch_rep<uint32_t, true>(b, st, n, r, g, ns, cp, s) : launch_rep<uint32_t, false>(b, st, n, r, g, ns, cp, s);
 }
 
+// ---------------------------------------------------------------- no-allocation variant
+// Some callers cannot allocate device memory themselves: applications whose
+// device memory is owned by another runtime's pool (a framework that reserves
+// the GPU up front), or loops that must not call cudaMalloc/cudaFree because
+// those calls can synchronise the whole device.  For them the table image of
+// the representative search lives in this file-scope array instead of a
+// per-call allocation.  Every GPU that loads the library holds it until exit.
+static constexpr size_t kStaticTableBytes = 224 * 1024;
+static __device__ __align__(256) uint8_t g_static_tables[kStaticTableBytes];
+
+// Device address of g_static_tables per device, looked up once per device
+// with that device current (the host-side name is only a stand-in).
+static uint8_t* static_tables_ptr(int dev, ed_status& st) {
+    static uint8_t* ptrs[256] = {nullptr};
+    st = ED_OK;
+    if (dev < 0 || dev >= 256) {
+        st = fail(ED_ERR_ARG, "device ordinal %d out of range", dev);
+        return nullptr;
+    }
+    if (!ptrs[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_static_tables);
+        if (e != cudaSuccess) {
+            st = cuda_fail(e, "cudaGetSymbolAddress(g_static_tables)");
+            return nullptr;
+        }
+        ptrs[dev] = (uint8_t*)p;
+    }
+    return ptrs[dev];
+}
+
+ed_status representatives_static(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
+                                 int32_t* nstab, uint8_t* compat, cudaStream_t s) {
+    if (!sector || n < 0 || (n > 0 && (!states || !rep || !g || !nstab || !compat)))
+        return fail(ED_ERR_ARG, "null argument");
+    ed_basis tmp;
+    ed_status st = build_host_tables(sector, tmp.ht);
+    if (st != ED_OK || n == 0) return st;
+    std::vector<uint8_t> image;
+    make_blob(tmp.ht, tmp.dt, image);
+    if (image.size() > kStaticTableBytes)
+        return fail(ED_ERR_TABLE_TOO_LARGE, "table image of %zu bytes exceeds the static limit of %zu bytes",
+                    image.size(), kStaticTableBytes);
+    int dev = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    uint8_t* base = static_tables_ptr(dev, st);
+    if (!base) return st;
+    tmp.word = tmp.ht.N <= 32 ? 4 : 8;
+    tmp.dt.blob = base;
+    ED_CUDA(cudaMemcpyAsync(base, image.data(), image.size(), cudaMemcpyHostToDevice, s));
+    // the kernel masks nothing: callers pass states of n_sites bits
+    return representatives_device(&tmp, states, n, rep, g, nstab, compat, s);
+}
+
 // ---------------------------------------------------------------- host
 void make_blob(const HostTables& t, DevTables& d, std::vector<uint8_t>& h) {
     const int S = 1 << t.m;

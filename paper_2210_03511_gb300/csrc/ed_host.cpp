@@ -494,6 +494,11 @@ ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, in
     return st;
 }
 
+ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep,
+                                     int32_t* g, int32_t* nstab, uint8_t* compat, ed_stream stream) {
+    return representatives_static(sector, states, n, rep, g, nstab, compat, (cudaStream_t)stream);
+}
+
 void ed_basis_free(ed_basis* b) {
     if (!b) return;
     b->alloc.put(b->reps.p, b->reps.bytes, 0);

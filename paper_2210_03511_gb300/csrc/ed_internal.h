@@ -155,6 +155,8 @@ ed_status upload_tables(ed_basis* b, cudaStream_t s);
 void make_blob(const HostTables& t, DevTables& d, std::vector<uint8_t>& image);
 ed_status representatives_device(const ed_basis* b, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
                                  int32_t* nstab, uint8_t* compat, cudaStream_t s);
+ed_status representatives_static(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
+                                 int32_t* nstab, uint8_t* compat, cudaStream_t s);
 // implemented in ed_apply.cu
 ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
 size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype dt);
