@@ -116,6 +116,23 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_aggregate(t_dev: float, t_e2e: float, work_local: float, device=None):
+    """Across ranks (independent replicas): the slowest rank's times and the summed work.
+
+    Each rank runs the whole workload on its own GPU (the path is replicated,
+    not sharded), so the job's throughput is the total work over the slowest
+    rank's time."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t_dev, t_e2e, work_local
+    tt = torch.tensor([t_dev, t_e2e], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ww = torch.tensor([work_local], dtype=torch.float64, device=device)
+    dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+    return float(tt[0]), float(tt[1]), float(ww[0])
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -276,11 +293,7 @@ def main():
     t_e2e = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / 1e3
     assert torch.equal(yh, y.cpu()), "e2e result differs from device-resident result"
     # aggregate over ranks (replicas)
-    if ws > 1:
-        tt = torch.tensor([t_dev, t_e2e], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_dev, t_e2e = tt.tolist()
-    work = D * n_terms * args.steps * ws
+    t_dev, t_e2e, work = replica_aggregate(t_dev, t_e2e, float(D * n_terms * args.steps), device=dev)
     value = work / t_dev / 1e9
     e2e = work / t_e2e / 1e9
     # roofline of the H.x kernel: algorithmic bytes per launch

@@ -2,22 +2,19 @@
 // matrix-vector multiply for a non-branching term", summed over all terms as in
 // Eq. branchingsum).
 //
-// Work decomposition.  A warp takes a batch of R consecutive rows.  For every
-// (row, flip term) pair it tests whether the term acts (the two spins differ)
-// with one ballot per 32 terms, and compacts the acting pairs into a per-warp
-// list in shared memory, ordered by row.  The list is then processed 32 items
-// per round, one item per lane, so no lane idles on a term that does not act
-// and rows of different length share rounds.  For an item, the image
+// Work decomposition.  One thread owns one row sigma_i (a grid-stride loop
+// over rows).  It builds the row's activity mask (flip term t acts iff its two
+// spins differ) and walks the set bits.  For an acting term the image
 // tau = sigma ^ mask is reduced to its representative by sublattice coding
 // (tables in shared memory), located by Limits + binary search, and
 // contributes
 //     conj(h) chi(g_tau) sqrt(|Stab tau~| / |Stab sigma_i|) x_j
 // to y_i: H is Hermitian, H_ij = conj(H_ji), and H_ji is the matrix element
-// of Eq. matrixelementrepresentatives with the conj(chi) reading.  Each row's
-// sum is formed by warp reductions over the lanes holding its items, in a
-// fixed order, and y_i is written once by the lane that owns row i: no
-// atomics, deterministic.  The Ising part is diagonal; it is counted with
-// ballots over the bonds of each coupling class.
+// of Eq. matrixelementrepresentatives with the conj(chi) reading.  The thread
+// accumulates its row alone and writes y_i once: no atomics, no cross-lane
+// reduction (FP64 arithmetic is scarce on this GPU), deterministic.  The
+// Ising part is diagonal: sum over pairs of J/4 (1 - 2 act), from popcounts of
+// the activity mask per coupling class.
 #include <algorithm>
 
 #include "ed_device.cuh"
@@ -56,27 +53,8 @@ template <> struct Val<2> { using T = double2; using R = double; static constexp
 template <> struct Val<3> { using T = float2; using R = float; static constexpr bool cplx = true; };
 
 constexpr int MAXV = 8;
-constexpr int ROWS = 4;           // rows per warp batch
 constexpr int BLOCK = 256;        // threads per block
-constexpr int WARPS = BLOCK / 32;
-
-template <typename R>
-__device__ __forceinline__ R warp_sum(R v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-template <typename W>
-__device__ __forceinline__ W shfl_w(W v, int src) {
-    if constexpr (sizeof(W) == 8) {
-        const uint32_t lo = __shfl_sync(0xffffffffu, (uint32_t)v, src);
-        const uint32_t hi = __shfl_sync(0xffffffffu, (uint32_t)(v >> 32), src);
-        return ((W)hi << 32) | (W)lo;
-    } else {
-        return __shfl_sync(0xffffffffu, v, src);
-    }
-}
+constexpr int MAXW = 8;           // activity mask words per row (n_flip <= 256)
 
 template <typename W, bool CH, int NS>
 __device__ __forceinline__ void rep_of(W tau, const TabView<CH>& t, W& r, int& g, int& nst, bool& cp) {
@@ -84,39 +62,46 @@ __device__ __forceinline__ void rep_of(W tau, const TabView<CH>& t, W& r, int& g
     else find_rep<W, CH>(tau, t, r, g, nst, cp);
 }
 
-// Shared layout: [table blob][flip terms][jhs table][jcls][diag positions]
-// [Limits directory][per-warp item lists].
+// Shared layout: [table blob][flip terms][packed (pa,pb)][jhs table][jcls]
+// [class masks][Limits directory].
 struct SmemLayout {
-    size_t flip, jhs, jcls, diag, dir, items, total;
-    int item_cap;
+    size_t flip, pab, jhs, jcls, cmask, dir, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(size_t blob, int n_flip, int n_jc, int G, int n_diag_bonds, int S) {
+__host__ __device__ inline SmemLayout smem_layout(size_t blob, int n_flip, int n_jc, int G, int S) {
     SmemLayout l;
     auto up16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
     l.flip = up16(blob);
-    l.jhs = up16(l.flip + (size_t)n_flip * sizeof(FlipTerm));
+    l.pab = up16(l.flip + (size_t)n_flip * sizeof(FlipTerm));
+    l.jhs = up16(l.pab + (size_t)n_flip * 2);
     l.jcls = up16(l.jhs + (size_t)n_jc * (G + 1) * 8);
-    l.diag = up16(l.jcls + (size_t)n_flip);
-    l.dir = up16(l.diag + 2 * (size_t)n_diag_bonds);
-    l.items = up16(l.dir + (size_t)(S + 1) * 4 + S);
-    l.item_cap = ROWS * n_flip;
-    l.total = up16(l.items + (size_t)WARPS * l.item_cap * 2);
+    l.cmask = up16(l.jcls + (size_t)n_flip);
+    l.dir = up16(l.cmask + (size_t)n_jc * MAXW * 4);
+    l.total = up16(l.dir + (size_t)(S + 1) * 4 + S);
     return l;
 }
 
 template <typename W, bool CH, int K, int NV, int NS>
-__global__ void __launch_bounds__(BLOCK) hx_kernel(HxArgs a) {
+__global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2) hx_kernel(HxArgs a) {
     using V = Val<K>;
     using T = typename V::T;
     using R = typename V::R;
     extern __shared__ __align__(16) uint8_t smem[];
-    const SmemLayout lay = smem_layout(a.dt.blob_bytes, a.n_flip, a.n_jc, a.dt.G, a.n_diag_bonds, a.S);
+    const SmemLayout lay = smem_layout(a.dt.blob_bytes, a.n_flip, a.n_jc, a.dt.G, a.S);
     stage_blob(smem, a.dt.blob, a.dt.blob_bytes);
     stage_blob(smem + lay.flip, (const uint8_t*)a.flips, (size_t)a.n_flip * sizeof(FlipTerm));
-    if (!V::cplx) stage_blob(smem + lay.jhs, (const uint8_t*)a.jhs, (size_t)a.n_jc * (a.dt.G + 1) * 8);
-    for (int i = threadIdx.x; i < a.n_flip; i += blockDim.x) smem[lay.jcls + i] = a.jcls[i];
-    for (int i = threadIdx.x; i < 2 * a.n_diag_bonds; i += blockDim.x) ((int8_t*)(smem + lay.diag))[i] = a.diag_pos[i];
+    stage_blob(smem + lay.jhs, (const uint8_t*)a.jhs, (size_t)a.n_jc * (a.dt.G + 1) * 8);
+    uint16_t* pab = (uint16_t*)(smem + lay.pab);
+    uint8_t* jcls = smem + lay.jcls;
+    uint32_t* cmask = (uint32_t*)(smem + lay.cmask);
+    for (int i = threadIdx.x; i < a.n_jc * MAXW; i += blockDim.x) cmask[i] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.n_flip; i += blockDim.x) {
+        const FlipTerm& f = ((const FlipTerm*)(smem + lay.flip))[i];
+        pab[i] = (uint16_t)((uint8_t)f.pa | ((uint16_t)(uint8_t)f.pb << 8));
+        jcls[i] = a.jcls[i];
+        atomicOr(&cmask[a.jcls[i] * MAXW + (i >> 5)], 1u << (i & 31));
+    }
     uint32_t* dir_base = (uint32_t*)(smem + lay.dir);
     uint8_t* dir_q = (uint8_t*)(dir_base + a.S + 1);
     for (int i = threadIdx.x; i <= a.S; i += blockDim.x) dir_base[i] = a.dir_base[i];
@@ -125,182 +110,144 @@ __global__ void __launch_bounds__(BLOCK) hx_kernel(HxArgs a) {
     const TabView<CH> t = tab_view<CH>(smem, a.dt);
     const FlipTerm* flips = (const FlipTerm*)(smem + lay.flip);
     const double* jhs = (const double*)(smem + lay.jhs);
-    const uint8_t* jcls = smem + lay.jcls;
-    const int8_t* dpos = (const int8_t*)(smem + lay.diag);
-    const int warp_in_block = threadIdx.x >> 5;
-    uint16_t* items = (uint16_t*)(smem + lay.items) + (size_t)warp_in_block * lay.item_cap;
     const W* __restrict__ reps = (const W*)a.reps;
     const T* __restrict__ x = (const T*)a.x;
     T* __restrict__ y = (T*)a.y;
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt_mask = (1u << lane) - 1u;
     const int64_t D = a.D;
     const int nvec = NV == 1 ? 1 : a.nvec;
     const int G1 = a.dt.G + 1;
-    const int64_t n_batches = (D + ROWS - 1) / ROWS;
-    const int64_t warp_global = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    const int nw = (a.n_flip + 31) >> 5;
     unsigned long long n_gather = 0, n_skip = 0, n_miss = 0;
-
-    for (int64_t batch = warp_global; batch < n_batches; batch += n_warps) {
-        const int64_t r0 = batch * ROWS;
-        const int nrows = (int)min((int64_t)ROWS, D - r0);
-        // lane r < nrows owns row r0 + r
-        W s_own = 0;
-        int stab_own = 1;
-        if (lane < nrows) {
-            s_own = reps[r0 + lane];
-            stab_own = a.stab[r0 + lane];
-        }
-        // ---- diagonal (Ising) part and the compacted list of acting flip terms
-        double diag_own = 0.0;
-        int n_items = 0;
-        for (int r = 0; r < nrows; ++r) {
-            const W s = shfl_w<W>(s_own, r);
-            double dg = 0.0;
-            for (int c = 0; c < a.n_diag_cls; ++c) {
-                const DiagClass dc = a.diag_cls[c];
-                int anti = 0;
-                for (int b0 = dc.first; b0 < dc.first + dc.count; b0 += 32) {
-                    const int b = b0 + lane;
-                    const bool ap = b < dc.first + dc.count &&
-                                    (((s >> dpos[2 * b]) ^ (s >> dpos[2 * b + 1])) & 1);
-                    anti += __popc(__ballot_sync(0xffffffffu, ap));
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < D; row += stride) {
+        const W s = reps[row];
+        const int stab_row = a.stab[row];
+        // activity mask: term t acts iff its two spins differ
+        uint32_t mask[MAXW];
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) mask[w] = 0u;
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            if (w < nw) {
+                const int tn = min(32, a.n_flip - 32 * w);
+                uint32_t mw = 0u;
+                for (int b = 0; b < tn; ++b) {
+                    const uint32_t e = pab[32 * w + b];
+                    mw |= (uint32_t)(((s >> (e & 0xFFu)) ^ (s >> (e >> 8))) & 1) << b;
                 }
-                dg += 0.25 * dc.J * (double)(dc.count - 2 * anti);
-            }
-            if (lane == r) diag_own = dg;
-            for (int t0 = 0; t0 < a.n_flip; t0 += 32) {
-                const int tt = t0 + lane;
-                bool act = false;
-                if (tt < a.n_flip) {
-                    const FlipTerm& ft = flips[tt];
-                    act = (((s >> ft.pa) ^ (s >> ft.pb)) & 1) != 0;
-                }
-                const uint32_t m = __ballot_sync(0xffffffffu, act);
-                if (act) items[n_items + __popc(m & lt_mask)] = (uint16_t)((r << 8) | tt);
-                n_items += __popc(m);
+                mask[w] = mw;
             }
         }
-        __syncwarp();
+        // Ising part: sum over pairs of J/4 (1 - 2 act) = sum_c jhalf_c (n_c/2 - popc(act & class_c))
+        double diag = 0.0;
+        for (int c = 0; c < a.n_jc; ++c) {
+            int nact = 0, ntot = 0;
+#pragma unroll
+            for (int w = 0; w < MAXW; ++w) {
+                if (w < nw) {
+                    const uint32_t cm = cmask[c * MAXW + w];
+                    nact += __popc(mask[w] & cm);
+                    ntot += __popc(cm);
+                }
+            }
+            diag += jhs[c * G1 + 1] * (0.5 * (double)ntot - (double)nact);
+        }
         R accr[NV], acci[NV];
 #pragma unroll
         for (int v = 0; v < NV; ++v) { accr[v] = 0; acci[v] = 0; }
-        // ---- rounds of 32 items
-        for (int base = 0; base < n_items; base += 32) {
-            const int j = base + lane;
-            const bool active = j < n_items;
-            const uint32_t item = active ? items[j] : 0u;
-            const int row = (int)(item >> 8);
-            const int tt = (int)(item & 0xFFu);
-            const W s = shfl_w<W>(s_own, row);
-            R vr[NV], vi[NV];
 #pragma unroll
-            for (int v = 0; v < NV; ++v) { vr[v] = 0; vi[v] = 0; }
-            if (active) {
-                const FlipTerm ft = flips[tt];
-                const W tau = s ^ (((W)1 << ft.pa) | ((W)1 << ft.pb));
+        for (int w = 0; w < MAXW; ++w) {
+            if (w >= nw) continue;
+            uint32_t mw = mask[w];
+            while (mw) {
+                const int tt = 32 * w + ctz32(mw);
+                mw &= mw - 1u;
+                const uint32_t e = pab[tt];
+                const W tau = s ^ (((W)1 << (e & 0xFFu)) | ((W)1 << (e >> 8)));
                 W rp;
                 int g, nst;
                 bool cp;
                 rep_of<W, CH, NS>(tau, t, rp, g, nst, cp);
                 if (!cp) {
                     ++n_skip;
-                } else {
-                    const int64_t jx = find_index<W>(rp, reps, dir_base, dir_q, a.limits, a.L);
-                    if (jx < 0) {
-                        ++n_miss;
-                    } else {
-                        ++n_gather;
-                        if constexpr (!V::cplx) {
-                            // jhalf * sqrt(n) from the table; real chi(g) = +-1 enters as a sign bit
-                            R c;
-                            if constexpr (K == 0) {
-                                const double cd = jhs[jcls[tt] * G1 + nst];
-                                c = __longlong_as_double(__double_as_longlong(cd) ^ ((long long)t.chi_neg[g] << 63));
-                            } else {
-                                c = (R)ft.jhalf * t.chif[g].x * t.sqrtnf[nst];
-                            }
-#pragma unroll
-                            for (int v = 0; v < NV; ++v)
-                                if (v < nvec) vr[v] = c * x[(int64_t)v * D + jx];
-                        } else {
-                            // h = jhalf + i sum_t k_t s^z_c (spin a down ? +1 : -1)
-                            double him = 0.0;
-                            if (ft.pc0 >= 0) him += ft.k0 * (((s >> ft.pc0) & 1) ? 0.5 : -0.5);
-                            if (ft.pc1 >= 0) him += ft.k1 * (((s >> ft.pc1) & 1) ? 0.5 : -0.5);
-                            if ((s >> ft.pa) & 1) him = -him;
-                            R cr, ci;
-                            if constexpr (K == 2) {
-                                const double2 ch = t.chi[g];
-                                const double sq = t.sqrtn[nst];
-                                // conj(h) chi = (jh - i him)(chr + i chi)
-                                cr = (ft.jhalf * ch.x + him * ch.y) * sq;
-                                ci = (ft.jhalf * ch.y - him * ch.x) * sq;
-                            } else {
-                                const float2 ch = t.chif[g];
-                                const float sq = t.sqrtnf[nst];
-                                const float jh = (float)ft.jhalf, hm = (float)him;
-                                cr = (jh * ch.x + hm * ch.y) * sq;
-                                ci = (jh * ch.y - hm * ch.x) * sq;
-                            }
-#pragma unroll
-                            for (int v = 0; v < NV; ++v)
-                                if (v < nvec) {
-                                    const T xj = x[(int64_t)v * D + jx];
-                                    vr[v] = cr * xj.x - ci * xj.y;
-                                    vi[v] = cr * xj.y + ci * xj.x;
-                                }
-                        }
-                    }
+                    continue;
                 }
-            }
-            // rows present in this round are contiguous: [first, last]
-            const int r_first = __shfl_sync(0xffffffffu, row, 0);
-            const int last_lane = min(31, n_items - 1 - base);
-            const int r_last = __shfl_sync(0xffffffffu, row, last_lane);
-            for (int rr = r_first; rr <= r_last; ++rr) {
-                const bool mine = active && row == rr;
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    if (v < nvec) {
-                        const R sr = warp_sum<R>(mine ? vr[v] : (R)0);
-                        if (lane == rr) accr[v] += sr;
-                        if constexpr (V::cplx) {
-                            const R si = warp_sum<R>(mine ? vi[v] : (R)0);
-                            if (lane == rr) acci[v] += si;
-                        }
+                const int64_t jx = find_index<W>(rp, reps, dir_base, dir_q, a.limits, a.L);
+                if (jx < 0) {
+                    ++n_miss;
+                    continue;
+                }
+                ++n_gather;
+                if constexpr (!V::cplx) {
+                    // jhalf * sqrt(n) from the table; real chi(g) = +-1 enters as a sign bit
+                    R c;
+                    if constexpr (K == 0) {
+                        const double cd = jhs[jcls[tt] * G1 + nst];
+                        c = __longlong_as_double(__double_as_longlong(cd) ^ ((long long)t.chi_neg[g] << 63));
+                    } else {
+                        c = (R)flips[tt].jhalf * t.chif[g].x * t.sqrtnf[nst];
                     }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        if (v < nvec) accr[v] += c * x[(int64_t)v * D + jx];
+                } else {
+                    const FlipTerm ft = flips[tt];
+                    // h = jhalf + i sum_t k_t s^z_c (spin a down ? +1 : -1)
+                    double him = 0.0;
+                    if (ft.pc0 >= 0) him += ft.k0 * (((s >> ft.pc0) & 1) ? 0.5 : -0.5);
+                    if (ft.pc1 >= 0) him += ft.k1 * (((s >> ft.pc1) & 1) ? 0.5 : -0.5);
+                    if ((s >> ft.pa) & 1) him = -him;
+                    R cr, ci;
+                    if constexpr (K == 2) {
+                        const double2 ch = t.chi[g];
+                        const double sq = t.sqrtn[nst];
+                        // conj(h) chi = (jh - i him)(chr + i chi)
+                        cr = (ft.jhalf * ch.x + him * ch.y) * sq;
+                        ci = (ft.jhalf * ch.y - him * ch.x) * sq;
+                    } else {
+                        const float2 ch = t.chif[g];
+                        const float sq = t.sqrtnf[nst];
+                        const float jh = (float)ft.jhalf, hm = (float)him;
+                        cr = (jh * ch.x + hm * ch.y) * sq;
+                        ci = (jh * ch.y - hm * ch.x) * sq;
+                    }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        if (v < nvec) {
+                            const T xj = x[(int64_t)v * D + jx];
+                            accr[v] += cr * xj.x - ci * xj.y;
+                            acci[v] += cr * xj.y + ci * xj.x;
+                        }
                 }
             }
         }
-        __syncwarp();
-        // ---- y_i = acc_i / sqrt(|Stab sigma_i|) + diag_i x_i
-        if (lane < nrows) {
-            const int64_t row_g = r0 + lane;
+        // y_i = acc_i / sqrt(|Stab sigma_i|) + diag_i x_i
 #pragma unroll
-            for (int v = 0; v < NV; ++v) {
-                if (v < nvec) {
-                    const int64_t o = (int64_t)v * D + row_g;
-                    if constexpr (!V::cplx) {
-                        const R inv = (K == 0) ? (R)t.isqrtn[stab_own] : (R)t.isqrtnf[stab_own];
-                        y[o] = accr[v] * inv + (R)diag_own * x[o];
-                    } else {
-                        const R inv = (K == 2) ? (R)t.isqrtn[stab_own] : (R)t.isqrtnf[stab_own];
-                        const T xi = x[o];
-                        T out;
-                        out.x = accr[v] * inv + (R)diag_own * xi.x;
-                        out.y = acci[v] * inv + (R)diag_own * xi.y;
-                        y[o] = out;
-                    }
+        for (int v = 0; v < NV; ++v) {
+            if (v < nvec) {
+                const int64_t o = (int64_t)v * D + row;
+                if constexpr (!V::cplx) {
+                    const R inv = (K == 0) ? (R)t.isqrtn[stab_row] : (R)t.isqrtnf[stab_row];
+                    y[o] = accr[v] * inv + (R)diag * x[o];
+                } else {
+                    const R inv = (K == 2) ? (R)t.isqrtn[stab_row] : (R)t.isqrtnf[stab_row];
+                    const T xi = x[o];
+                    T out;
+                    out.x = accr[v] * inv + (R)diag * xi.x;
+                    out.y = acci[v] * inv + (R)diag * xi.y;
+                    y[o] = out;
                 }
             }
         }
     }
-    n_gather = warp_sum<unsigned long long>(n_gather);
-    n_skip = warp_sum<unsigned long long>(n_skip);
-    n_miss = warp_sum<unsigned long long>(n_miss);
-    if (lane == 0) {
+    // counters: one atomic per warp
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        n_gather += __shfl_xor_sync(0xffffffffu, n_gather, o);
+        n_skip += __shfl_xor_sync(0xffffffffu, n_skip, o);
+        n_miss += __shfl_xor_sync(0xffffffffu, n_miss, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
         if (n_gather) atomicAdd(a.counters + 0, n_gather);
         if (n_skip) atomicAdd(a.counters + 1, n_skip);
         if (n_miss) atomicAdd(a.counters + 2, n_miss);
@@ -309,7 +256,7 @@ __global__ void __launch_bounds__(BLOCK) hx_kernel(HxArgs a) {
 
 static SmemLayout layout_for(const ed_hamiltonian* h) {
     const ed_basis* b = h->basis;
-    return smem_layout(b->dt.blob_bytes, h->n_flip, h->n_jc, b->dt.G, h->n_diag_bonds, 1 << b->ht.m);
+    return smem_layout(b->dt.blob_bytes, h->n_flip, h->n_jc, b->dt.G, 1 << b->ht.m);
 }
 
 size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype) { return layout_for(h).total; }
@@ -328,8 +275,7 @@ static ed_status launch(const HxArgs& a, size_t smem, cudaStream_t s) {
         cfg_smem = (int)smem;
         cfg_grid = sms * per_sm;
     }
-    const int64_t batches = (a.D + ROWS - 1) / ROWS;
-    int64_t grid = std::min<int64_t>(cfg_grid, (batches + WARPS - 1) / WARPS);
+    int64_t grid = std::min<int64_t>(cfg_grid, (a.D + BLOCK - 1) / BLOCK);
     if (grid < 1) grid = 1;
     k<<<(unsigned)grid, BLOCK, smem, s>>>(a);
     ED_CUDA(cudaGetLastError());

@@ -516,14 +516,14 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
             v_lo[v] = next;
         }
     }
-    // two-level Limits: q_v bits for top value v so buckets hold ~16 states
+    // two-level Limits: q_v bits for top value v so buckets hold ~4 states
     std::vector<uint32_t> seg_base(S + 1, 0);
     std::vector<uint8_t> seg_q(S, 0);
     uint64_t keys = 0;
     for (int v = 0; v < S; ++v) {
         const uint64_t Dv = v_lo[v + 1] - v_lo[v];
         int q = 0;
-        while (q < L && (Dv >> q) > 16) ++q;
+        while (q < L && (Dv >> q) > 4) ++q;
         seg_q[v] = (uint8_t)q;
         seg_base[v] = (uint32_t)keys;
         keys += (uint64_t)1 << q;

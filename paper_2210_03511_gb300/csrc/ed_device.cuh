@@ -12,6 +12,14 @@
 
 namespace ed {
 
+ED_HD int ctz32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __ffs((int)v) - 1;
+#else
+    return __builtin_ctz(v);
+#endif
+}
+
 template <typename T>
 ED_HD T ld_ro(const T* p) {
 #ifdef __CUDA_ARCH__
@@ -151,11 +159,13 @@ ED_HD void find_rep(W s, const TabView<CHUNKED>& t, W& rep, int& gbest, int& nst
     compat = cp;
 }
 
-// find_rep for a compile-time number of blocks NS (2..4): substates and
-// block representatives live in registers; every candidate g composes its
-// full image from its source blocks in one pass (one 8-byte load of the packed
-// (dest block, map id) entries, NS map lookups), so candidates cost the same
-// and lanes stay converged.  Same outputs as find_rep.
+// find_rep for a compile-time number of blocks NS (2..4).  Substates, block
+// representatives and the best image so far (block by block) live in
+// registers.  Each candidate g reads its packed (source block, map id)
+// entries for all destination blocks with one 8-byte load and composes its
+// image from the most significant destination block down, stopping at the
+// first block that exceeds the best image (most candidates stop after one
+// lookup).  Same outputs as find_rep.
 template <typename W, bool CHUNKED, int NS>
 ED_HD void find_rep_ns(W s, const TabView<CHUNKED>& t, W& rep, int& gbest, int& nstab, bool& compat) {
     static_assert(NS >= 2 && NS <= 4, "specialised for 2..4 blocks");
@@ -169,33 +179,63 @@ ED_HD void find_rep_ns(W s, const TabView<CHUNKED>& t, W& rep, int& gbest, int& 
         r[X] = t.rep[X * S + sub[X]];
         minrep = r[X] < minrep ? r[X] : minrep;
     }
-    W best = ~(W)0;
+    uint32_t bestb[NS];
+#pragma unroll
+    for (int Z = 0; Z < NS; ++Z) bestb[Z] = 0xFFFFFFFFu;
+    bestb[0] = minrep;
+    bool have = false;
     int gb = 0, ns = 0;
     bool cp = true;
     uint32_t cls = 0;
+    // One flat loop over the concatenated Sym_Y lists of all blocks Y with
+    // Rep_Y = MinRep: a separate loop per Y would make a warp wait for the
+    // longest list of every Y in turn.
+    uint32_t ymask = 0;
 #pragma unroll
-    for (int Y = 0; Y < NS; ++Y) {
-        if (r[Y] != minrep) continue;
-        const uint32_t q0 = t.sym_off[Y * (S + 1) + sub[Y]], q1 = t.sym_off[Y * (S + 1) + sub[Y] + 1];
-        for (uint32_t q = q0; q < q1; ++q) {
-            const int g = t.sym_ids[q];
-            const uint2 pk = *(const uint2*)(t.dl + (size_t)g * 4);
-            const uint32_t ent[4] = {pk.x & 0xFFFFu, pk.x >> 16, pk.y & 0xFFFFu, pk.y >> 16};
-            W img = 0;
+    for (int Y = 0; Y < NS; ++Y) ymask |= (r[Y] == minrep ? 1u : 0u) << Y;
+    uint32_t q = 0, q1 = 0;
+    while (true) {
+        if (q == q1) {
+            if (!ymask) break;
+            const int Y = ctz32(ymask);
+            ymask &= ymask - 1;
+            uint32_t sy = sub[0];
 #pragma unroll
-            for (int X = 0; X < NS; ++X) {
-                const uint32_t Z = ent[X] >> 12;
-                const uint32_t v = sym_action<CHUNKED>(t, ent[X] & 0xFFFu, sub[X]);
-                img |= (W)v << (m * (NS - 1 - (int)Z));
-            }
-            if (img < best) {
-                best = img; gb = g; ns = 1; cls = t.chi_cls[g]; cp = true;
-            } else if (img == best) {
-                ++ns;
-                cp = cp && (t.chi_cls[g] == cls);
-            }
+            for (int k = 1; k < NS; ++k) sy = (Y == k) ? sub[k] : sy;
+            q = t.sym_off[Y * (S + 1) + sy];
+            q1 = t.sym_off[Y * (S + 1) + sy + 1];
+            continue;
+        }
+        const int g = t.sym_ids[q++];
+        const uint2 pk = *(const uint2*)(t.dl + (size_t)g * 4);
+        const uint32_t ent[4] = {pk.x & 0xFFFFu, pk.x >> 16, pk.y & 0xFFFFu, pk.y >> 16};
+        uint32_t v[NS];
+        v[0] = minrep;
+        int state = have ? 0 : -1;  // 0: equal so far, -1: smaller, 1: larger
+#pragma unroll
+        for (int Z = 1; Z < NS; ++Z) {
+            if (state == 1) break;
+            const uint32_t X = ent[Z] >> 12;
+            uint32_t sx = sub[0];
+#pragma unroll
+            for (int k = 1; k < NS; ++k) sx = (X == (uint32_t)k) ? sub[k] : sx;
+            v[Z] = sym_action<CHUNKED>(t, ent[Z] & 0xFFFu, sx);
+            if (state == 0) state = v[Z] > bestb[Z] ? 1 : (v[Z] < bestb[Z] ? -1 : 0);
+        }
+        if (state == 1) continue;
+        if (state == -1) {
+#pragma unroll
+            for (int Z = 1; Z < NS; ++Z) bestb[Z] = v[Z];
+            have = true;
+            gb = g; ns = 1; cls = t.chi_cls[g]; cp = true;
+        } else {
+            ++ns;
+            cp = cp && (t.chi_cls[g] == cls);
         }
     }
+    W best = 0;
+#pragma unroll
+    for (int Z = 0; Z < NS; ++Z) best = (best << m) | (W)bestb[Z];
     rep = best;
     gbest = gb;
     nstab = ns;

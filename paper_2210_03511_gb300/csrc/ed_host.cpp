@@ -240,7 +240,7 @@ ed_status build_host_tables(const ed_sector* sec, HostTables& t) {
             for (int Z = 0; Z < n_sub; ++Z) {
                 const uint32_t e = t.srclid[(size_t)g * n_sub + Z];
                 const int X = (int)(e & 0xFFu), lid = (int)(e >> 8);
-                t.dl[(size_t)g * t.dl_stride + X] = (uint16_t)((Z << 12) | lid);
+                t.dl[(size_t)g * t.dl_stride + Z] = (uint16_t)((X << 12) | lid);
             }
     }
     t.chi_neg.assign(G, 0);

@@ -61,9 +61,9 @@ struct HostTables {
     // tables (high m - c and low c = m/2 bits) of uint16 images that are OR-ed.
     int n_lmap = 0;
     std::vector<uint32_t> srclid;   // [G][n_sub]
-    // Per element and SOURCE block X: (dest block Z << 12) | map id, padded to
-    // dl_stride (a multiple of 4) entries per element; empty when a map id does
-    // not fit 12 bits or there are more than 16 blocks.
+    // Per element and DESTINATION block Z: (source block X << 12) | map id,
+    // padded to dl_stride (a multiple of 4) entries per element; empty when a
+    // map id does not fit 12 bits or there are more than 16 blocks.
     std::vector<uint16_t> dl;
     int dl_stride = 0;
     std::vector<uint8_t> chi_neg;   // [G] real chi(g) < 0

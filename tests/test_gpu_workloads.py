@@ -1,0 +1,137 @@
+"""Full-size workloads: parity of the CUDA path with the oracle on sampled
+outputs plus properties that hold at any size.
+
+Basis (bit-exact set equality by a counting argument): the GPU dimension
+equals the character-formula dimension (computed without enumeration), the
+GPU basis is strictly increasing, every sampled GPU state is its own orbit
+minimum with the right stabilizer and a non-zero projector (oracle brute
+force), and every compatible representative of oracle-drawn random states is
+present.  Sorted + all members valid + right count => the sets are equal.
+
+H.x: x_j = keyed SplitMix64 uniform of state_j; the oracle evaluates
+y(sigma) = sum_j H[sigma, j] x(state_j) for representatives it draws itself
+(matrix-free, brute-force representatives), compared with the GPU y at the
+index of sigma.  Tolerance: 64 eps * R with R = sum_b |J_b| (1/4 + sqrt|G|/2)
+(+ the chirality terms), a bound on |H| |x| for |x_j| <= 1; FP32 vectors use
+eps_32 and add the rounding of x.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from edinputs import configs as C
+from edinputs.vectors import state_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_03511_gb300 import build
+    build.build()
+    import paper_2210_03511_gb300 as pkg
+    return pkg
+
+
+def _random_reps(problem, n, seed):
+    rng = np.random.default_rng(seed)
+    s = problem.sector
+    N, n_up = s.n_sites, s.n_up
+    out = []
+    tries = 0
+    while len(out) < n and tries < 200 * n:
+        tries += 1
+        bits = np.zeros(N, dtype=np.int64)
+        bits[rng.choice(N, n_up, replace=False)] = 1
+        st = int("".join(map(str, bits)), 2)
+        r, g, ns, ssum = oracle.rep(s, st)
+        if abs(ssum) > 1e-9:
+            out.append(r)
+    return np.array(sorted(set(out)), dtype=np.uint64)
+
+
+def _bound(problem, eps):
+    G = problem.sector.n_sym
+    R = np.sum(np.abs(problem.terms.J)) * (0.25 + 0.5 * np.sqrt(G))
+    if len(problem.terms.tris):
+        R += np.sum(np.abs(problem.terms.Jchi)) * 3 * 0.25 * np.sqrt(G)
+    return 64 * eps * R
+
+
+def _check_basis(P, problem, n_sample, seed):
+    s = problem.sector
+    b = P.Basis(s)
+    D = b.dim
+    assert D == oracle.sector_dim_formula(s)
+    reps, stab = b.export()
+    assert np.all(reps[1:] > reps[:-1])
+    rng = np.random.default_rng(seed)
+    idx = rng.choice(D, size=min(n_sample, D), replace=False)
+    for i in idx:
+        r, g, ns, ssum = oracle.rep(s, int(reps[i]))
+        assert r == int(reps[i]) and ns == int(stab[i]) and abs(ssum) > 1e-9
+    drawn = _random_reps(problem, n_sample // 4, seed + 1)
+    pos = np.searchsorted(reps, drawn)
+    assert np.all(pos < D) and np.array_equal(reps[pos], drawn)
+    return b, reps, drawn, pos
+
+
+def _check_hx(P, problem, b, reps, drawn, pos, dtype, seed=9):
+    import torch
+    cplx = dtype in (torch.complex64, torch.complex128)
+    X = state_vector(seed, reps, complex_=cplx)
+    x = torch.tensor(X, device="cuda").to(dtype)
+    y = torch.empty_like(x)
+    h = P.Hamiltonian(b, problem.terms)
+    h.apply(x, y)
+    torch.cuda.synchronize()
+    yg = y[torch.tensor(pos.astype(np.int64), device="cuda")].cpu().numpy().astype(np.complex128)
+    single = dtype in (torch.float32, torch.complex64)
+    if single:
+        # the oracle uses the FP64 keyed x; FP32 rounding of x adds eps_32 relative per term
+        eps = np.finfo(np.float32).eps
+    else:
+        eps = np.finfo(np.float64).eps
+    yo = oracle.rows(problem, drawn, seed, cplx)
+    err = np.abs(yg - yo)
+    bound = _bound(problem, eps) * (4 if single else 1)
+    assert np.all(err <= bound), (err.max(), bound)
+    return h
+
+
+def test_square32_bench_config(P):
+    """The benchmark's workload and launch configuration (FP64 ed_apply)."""
+    import torch
+    p = C.square32()
+    b, reps, drawn, pos = _check_basis(P, p, 3000, 1)
+    _check_hx(P, p, b, reps, drawn, pos, torch.float64)
+    _check_hx(P, p, b, reps, drawn, pos, torch.float32)
+
+
+def test_square32_other_sectors(P):
+    """Gamma.B2 and M.A2 sectors (characters -1 on mirrors / translations)."""
+    import torch
+    for irrep, mom in (("B2", "Gamma"), ("A2", "M")):
+        p = C.square32(irrep, mom)
+        b, reps, drawn, pos = _check_basis(P, p, 800, 3)
+        _check_hx(P, p, b, reps, drawn, pos, torch.float64)
+
+
+def test_kagome36_chiral(P):
+    """Complex Hamiltonian (scalar chirality), 64-bit state words, 12-site blocks."""
+    import torch
+    p = C.kagome36()
+    b, reps, drawn, pos = _check_basis(P, p, 600, 5)
+    _check_hx(P, p, b, reps, drawn, pos, torch.complex64)
+    _check_hx(P, p, b, reps, drawn, pos, torch.complex128)
+
+
+def test_square40_scale(P):
+    """The largest workload: N = 40, T40 x C4 x Z2 (320 elements), D ~ 4.3e8, FP32 vectors."""
+    import torch
+    p = C.square40()
+    b, reps, drawn, pos = _check_basis(P, p, 400, 7)
+    _check_hx(P, p, b, reps, drawn, pos, torch.float32)
