@@ -97,3 +97,29 @@ def triangular24(k=(0.0, 0.0), irrep="A1"):
 def square40(spinflip=1, irrep="A"):
     """40-site square cluster a1=(6,2), a2=(-2,6); J1=1, J2=0.55; T40 x C4 x Z2 (320)."""
     return square([[6, 2], [-2, 6]], 1.0, 0.55, irrep=irrep, point="full", spinflip=spinflip)
+
+
+def all_sectors(kind: str, P, J1=1.0, J2=0.0, *, n_sublat: int, n_up=None, point="full", max_table_bytes=96 * 1024):
+    """Every (k, rho_k) sector of a square or triangular torus: each allowed
+    momentum with every 1-D irrep of its little group.  Sectors share one site
+    numbering (the sublattice count is fixed)."""
+    from .lattice import allowed_momenta, little_group_irreps
+    lat = {"square": square_lattice, "triangular": triangular_lattice}[kind]()
+    make = {"square": square, "triangular": triangular}[kind]
+    cl = Cluster(lat, P)
+    out = []
+    for k in allowed_momenta(cl):
+        for irr in little_group_irreps(cl, k, point=point):
+            p = make(P, J1, J2, k=tuple(k), irrep=irr, n_sublat=n_sublat, n_up=n_up, point=point,
+                     max_table_bytes=max_table_bytes)
+            p.meta["sector"] = f"k=({k[0]:.3f},{k[1]:.3f}) {irr}"
+            out.append(p)
+    return out
+
+
+def triangular24_sectors(J2=0.125, max_table_bytes=96 * 1024):
+    """Every (k, rho_k) sector of the 24-site triangular torus (a1=(5,1), a2=(4,-4)),
+    J1=1, J2=0.125, Sz=0: 24 momenta, each with the 1-D irreps of its little
+    group inside C2v (36 sectors).  Every sector uses the same site numbering
+    (2 blocks of 12 sites)."""
+    return all_sectors("triangular", [[5, 1], [4, -4]], 1.0, J2, n_sublat=2, max_table_bytes=max_table_bytes)

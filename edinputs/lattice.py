@@ -645,3 +645,42 @@ def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: i
     meta = dict(k=k.tolist(), irrep=irrep, spinflip=spinflip, n_cells=cl.n_cells,
                 n_basis=cl.lat.n_basis, point_ops=[o[0] for o in lops], positions=cl.pos[order].tolist())
     return Problem(name, sector, terms.relabel(new_of_old), meta)
+
+
+# --------------------------------------------------------------------------
+# all sectors of a cluster
+# --------------------------------------------------------------------------
+def allowed_momenta(cl: Cluster) -> list[np.ndarray]:
+    """Momenta k with k.p in 2 pi Z for the periodicity vectors, one per class
+    modulo the reciprocal Bravais lattice (as many as unit cells)."""
+    Pc = cl.cart_periods()
+    Pinv = np.linalg.inv(Pc)
+    Bt = 2 * np.pi * np.linalg.inv(cl.lat.A).T
+    Btinv = np.linalg.inv(Bt)
+    out = []
+    R = cl.n_cells
+    for n1 in range(-R, R + 1):
+        for n2 in range(-R, R + 1):
+            k = 2 * np.pi * (Pinv @ np.array([n1, n2], dtype=float))
+            f = k @ Btinv
+            f = f - np.floor(f + 1e-9)
+            kk = f @ Bt
+            if not any(np.allclose(kk, q, atol=1e-8) for q in out):
+                out.append(kk)
+    if len(out) != cl.n_cells:
+        raise RuntimeError("momentum enumeration failed")
+    return out
+
+
+def little_group_irreps(cl: Cluster, k, point: str = "full") -> list[str]:
+    """Names of the 1-D irreps of the little group of k (within the chosen point group)."""
+    sg = space_group(cl, point=point, translations=True)
+    sg.point_ops = [sg.point_ops[i] for i in sorted(set(sg.pidx.tolist()))]
+    k = np.asarray(k, dtype=float)
+    Bt = 2 * np.pi * np.linalg.inv(cl.lat.A).T
+    little = []
+    for oi, (label, O, order, ang) in enumerate(sg.point_ops):
+        f = (O @ k - k) @ np.linalg.inv(Bt)
+        if np.all(np.abs(f - np.round(f)) < 1e-6):
+            little.append(sg.point_ops[oi])
+    return [n for n, _ in one_d_irreps(little)]

@@ -253,6 +253,69 @@ typedef struct {
 ed_status ed_lanczos(const ed_hamiltonian* h, const ed_lanczos_opts* opts, double* evals, void* evecs,
                      ed_lanczos_report* report, ed_stream stream);
 
+/* ---------------------------------------------------------------- batches of sectors
+ * A batch groups Hamiltonians of several sectors of one cluster (same number
+ * of sites, state word and sublattice blocks, e.g. every momentum/irrep
+ * sector) so that one launch applies all of them and block Lanczos runs on
+ * all of them at once.  Vectors of a batch are concatenated: sector s owns rows
+ * [row_off[s], row_off[s+1]) (ed_batch_rows), and a block of nvec vectors of
+ * sector s starts at element nvec*row_off[s], column-major within the sector.
+ * The Hamiltonians must outlive the batch. */
+typedef struct ed_batch ed_batch;
+
+ed_status ed_batch_create(const ed_hamiltonian* const* h, int32_t n, ed_batch** out);
+
+/* HOST row_off[n+1]. */
+ed_status ed_batch_rows(const ed_batch* batch, int64_t* row_off);
+
+/* y_s = H_s x_s for every sector s, nvec (1..8) vectors each, in one persistent
+ * launch: every block takes a contiguous range of the batch's rows and stages
+ * each sector's tables as it reaches its rows.  x, y: DEVICE, caller-owned.
+ * Asynchronous on `stream`. */
+ed_status ed_apply_batch(const ed_batch* batch, ed_dtype dtype, const void* x, void* y, int32_t nvec, ed_stream stream);
+
+/* Time ed_apply_batch for grids of 1, 2, 4, 8, 16 waves of resident blocks
+ * (shorter row ranges per block balance uneven sectors, longer ones restage
+ * fewer tables) and keep the fastest for this dtype and nvec.  Overwrites y.
+ * Synchronous; call it before capturing work that uses the batch. */
+ed_status ed_batch_autotune(ed_batch* batch, ed_dtype dtype, const void* x, void* y, int32_t nvec, ed_stream stream,
+                            int32_t* waves);
+
+void ed_batch_free(ed_batch* batch);
+
+typedef struct {
+    ed_dtype dtype;        /* ED_F64 (all sectors real) or ED_C128 */
+    int32_t block;         /* right-hand sides per sector, 1..8 */
+    int32_t n_eig;         /* lowest eigenvalues per sector */
+    double tol;            /* relative change of each eigenvalue between checks */
+    int32_t max_iter;      /* block steps at most (2..400) */
+    uint64_t seed;         /* Gaussian start blocks from keyed SplitMix64 of (seed, column, state) */
+    int32_t use_graph;     /* 1: capture one step (all kernels, all sectors) as a CUDA graph and replay it */
+    int32_t check_every;   /* eigenvalue check every this many steps */
+} ed_block_lanczos_opts;
+
+typedef struct {
+    int32_t iters;             /* block steps taken */
+    int32_t converged_sectors; /* sectors whose n_eig values were steady for two checks */
+    int32_t krylov_dim;        /* iters * block */
+    int32_t used_graph;
+    double seconds;            /* wall time of the call */
+    double step_seconds;       /* time inside the steps (graph launches + sync) */
+} ed_block_lanczos_report;
+
+/* ed_lanczos_batch -- block Lanczos (the block form of Eqs.
+ * lanczosrecursionabbrev and tmatrix with b x b blocks) on every sector of the
+ * batch at once, with full reorthogonalisation (classical Gram-Schmidt twice
+ * against all stored blocks) and Cholesky QR twice for the new block; inner
+ * products in FP64 with a fixed reduction order.  evals: HOST [n][n_eig]
+ * (sector-major), lowest eigenvalues of each sector's block tridiagonal T
+ * (degenerate eigenvalues appear with their multiplicity up to the block size).
+ * Workspace from the batch's allocator (or cudaMalloc), released before
+ * return.  Synchronous (uses an internal stream).  ED_ERR_NOT_CONVERGED if
+ * some sector did not settle within max_iter (values still written). */
+ed_status ed_lanczos_batch(const ed_batch* batch, const ed_block_lanczos_opts* opts, double* evals,
+                           ed_block_lanczos_report* report, ed_stream stream);
+
 /* Message of the last error on the calling thread ("" if none). */
 const char* ed_last_error(void);
 

@@ -11,7 +11,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libed.so")
-SOURCES = ["ed_host.cpp", "ed_basis.cu", "ed_apply.cu", "ed_lanczos.cu"]
+SOURCES = ["ed_host.cpp", "ed_basis.cu", "ed_apply.cu", "ed_apply_k0.cu", "ed_apply_k1.cu", "ed_apply_k2.cu",
+           "ed_apply_k3.cu", "ed_lanczos.cu", "ed_batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,0 +1,386 @@
+// y = H x in the symmetry-adapted basis (pull form of Alg. "Parallel
+// matrix-vector multiply for a non-branching term", summed over all terms as in
+// Eq. branchingsum).
+//
+// Work decomposition.  One thread owns one row sigma_i (a grid-stride loop
+// over rows).  It builds the row's activity mask (flip term t acts iff its two
+// spins differ) and walks the set bits.  For an acting term the image
+// tau = sigma ^ mask is reduced to its representative by sublattice coding
+// (tables in shared memory), located by Limits + binary search, and
+// contributes
+//     conj(h) chi(g_tau) sqrt(|Stab tau~| / |Stab sigma_i|) x_j
+// to y_i: H is Hermitian, H_ij = conj(H_ji), and H_ji is the matrix element
+// of Eq. matrixelementrepresentatives with the conj(chi) reading.  The thread
+// accumulates its row alone and writes y_i once: no atomics, no cross-lane
+// reduction (FP64 arithmetic is scarce on this GPU), deterministic.  The
+// Ising part is diagonal: sum over pairs of J/4 (1 - 2 act), from popcounts of
+// the activity mask per coupling class.
+// Templates of the H.x kernels, instantiated per value kind in
+// ed_apply_k<K>.cu (one translation unit per kind so they compile in parallel).
+#pragma once
+
+#include <algorithm>
+#include <type_traits>
+
+#include "ed_device.cuh"
+#include "ed_internal.h"
+
+namespace ed {
+
+template <int K> struct Val;
+template <> struct Val<0> { using T = double; using R = double; static constexpr bool cplx = false; };
+template <> struct Val<1> { using T = float; using R = float; static constexpr bool cplx = false; };
+template <> struct Val<2> { using T = double2; using R = double; static constexpr bool cplx = true; };
+template <> struct Val<3> { using T = float2; using R = float; static constexpr bool cplx = true; };
+
+constexpr int MAXV = 8;
+constexpr int BLOCK = 256;        // threads per block
+constexpr int MAXW = 8;           // activity mask words per row (n_flip <= 256)
+
+template <typename W, bool CH, int NS>
+__device__ __forceinline__ void rep_of(W tau, const TabView<CH>& t, W& r, int& g, int& nst, bool& cp) {
+    if constexpr (NS >= 2 && NS <= 4) find_rep_ns<W, CH, NS>(tau, t, r, g, nst, cp);
+    else find_rep<W, CH>(tau, t, r, g, nst, cp);
+}
+
+// Shared layout: [table blob][flip terms][packed (pa,pb)][jhs table][jcls]
+// [class masks][Limits directory].
+struct SmemLayout {
+    size_t flip, pab, jhs, jcls, cmask, dir, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(size_t blob, int n_flip, int n_jc, int G, int S) {
+    SmemLayout l;
+    auto up16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
+    l.flip = up16(blob);
+    l.pab = up16(l.flip + (size_t)n_flip * sizeof(FlipTerm));
+    l.jhs = up16(l.pab + (size_t)n_flip * 2);
+    l.jcls = up16(l.jhs + (size_t)n_jc * (G + 1) * 8);
+    l.cmask = up16(l.jcls + (size_t)n_flip);
+    l.dir = up16(l.cmask + (size_t)n_jc * MAXW * 4);
+    l.total = up16(l.dir + (size_t)(S + 1) * 4 + S);
+    return l;
+}
+
+struct Counts {
+    unsigned long long gather = 0, skip = 0, miss = 0;
+};
+
+// Stage one sector's tables into shared memory and process rows
+// first, first + stride, ... < end of that sector.  All threads of the block
+// must call it (it synchronises the block).
+template <typename W, bool CH, int K, int NV, int NS>
+__device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t first, int64_t end, int64_t stride,
+                                        Counts& cnt) {
+    using V = Val<K>;
+    using T = typename V::T;
+    using R = typename V::R;
+    const SmemLayout lay = smem_layout(a.dt.blob_bytes, a.n_flip, a.n_jc, a.dt.G, a.S);
+    stage_blob(smem, a.dt.blob, a.dt.blob_bytes);
+    stage_blob(smem + lay.flip, (const uint8_t*)a.flips, (size_t)a.n_flip * sizeof(FlipTerm));
+    stage_blob(smem + lay.jhs, (const uint8_t*)a.jhs, (size_t)a.n_jc * (a.dt.G + 1) * 8);
+    uint16_t* pab = (uint16_t*)(smem + lay.pab);
+    uint8_t* jcls = smem + lay.jcls;
+    uint32_t* cmask = (uint32_t*)(smem + lay.cmask);
+    for (int i = threadIdx.x; i < a.n_jc * MAXW; i += blockDim.x) cmask[i] = 0u;
+    __syncthreads();
+    for (int i = threadIdx.x; i < a.n_flip; i += blockDim.x) {
+        const FlipTerm& f = ((const FlipTerm*)(smem + lay.flip))[i];
+        pab[i] = (uint16_t)((uint8_t)f.pa | ((uint16_t)(uint8_t)f.pb << 8));
+        jcls[i] = a.jcls[i];
+        atomicOr(&cmask[a.jcls[i] * MAXW + (i >> 5)], 1u << (i & 31));
+    }
+    uint32_t* dir_base = (uint32_t*)(smem + lay.dir);
+    uint8_t* dir_q = (uint8_t*)(dir_base + a.S + 1);
+    for (int i = threadIdx.x; i <= a.S; i += blockDim.x) dir_base[i] = a.dir_base[i];
+    for (int i = threadIdx.x; i < a.S; i += blockDim.x) dir_q[i] = a.dir_q[i];
+    __syncthreads();
+    const TabView<CH> t = tab_view<CH>(smem, a.dt);
+    const FlipTerm* flips = (const FlipTerm*)(smem + lay.flip);
+    const double* jhs = (const double*)(smem + lay.jhs);
+    const W* __restrict__ reps = (const W*)a.reps;
+    const T* __restrict__ x = (const T*)a.x;
+    T* __restrict__ y = (T*)a.y;
+    const int64_t D = a.D;
+    const int nvec = NV == 1 ? 1 : a.nvec;
+    const int G1 = a.dt.G + 1;
+    const int nw = (a.n_flip + 31) >> 5;
+    unsigned long long n_gather = 0, n_skip = 0, n_miss = 0;
+    for (int64_t row = first; row < end; row += stride) {
+        const W s = reps[row];
+        const int stab_row = a.stab[row];
+        // activity mask: term t acts iff its two spins differ
+        uint32_t mask[MAXW];
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) mask[w] = 0u;
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            if (w < nw) {
+                const int tn = min(32, a.n_flip - 32 * w);
+                uint32_t mw = 0u;
+                for (int b = 0; b < tn; ++b) {
+                    const uint32_t e = pab[32 * w + b];
+                    mw |= (uint32_t)(((s >> (e & 0xFFu)) ^ (s >> (e >> 8))) & 1) << b;
+                }
+                mask[w] = mw;
+            }
+        }
+        // Ising part: sum over pairs of J/4 (1 - 2 act) = sum_c jhalf_c (n_c/2 - popc(act & class_c))
+        double diag = 0.0;
+        for (int c = 0; c < a.n_jc; ++c) {
+            int nact = 0, ntot = 0;
+#pragma unroll
+            for (int w = 0; w < MAXW; ++w) {
+                if (w < nw) {
+                    const uint32_t cm = cmask[c * MAXW + w];
+                    nact += __popc(mask[w] & cm);
+                    ntot += __popc(cm);
+                }
+            }
+            diag += jhs[c * G1 + 1] * (0.5 * (double)ntot - (double)nact);
+        }
+        R accr[NV], acci[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { accr[v] = 0; acci[v] = 0; }
+#pragma unroll
+        for (int w = 0; w < MAXW; ++w) {
+            if (w >= nw) continue;
+            uint32_t mw = mask[w];
+            while (mw) {
+                const int tt = 32 * w + ctz32(mw);
+                mw &= mw - 1u;
+                const uint32_t e = pab[tt];
+                const W tau = s ^ (((W)1 << (e & 0xFFu)) | ((W)1 << (e >> 8)));
+                W rp;
+                int g, nst;
+                bool cp;
+                rep_of<W, CH, NS>(tau, t, rp, g, nst, cp);
+                if (!cp) {
+                    ++n_skip;
+                    continue;
+                }
+                const int64_t jx = find_index<W>(rp, reps, dir_base, dir_q, a.limits, a.L);
+                if (jx < 0) {
+                    ++n_miss;
+                    continue;
+                }
+                ++n_gather;
+                if constexpr (!V::cplx) {
+                    // jhalf * sqrt(n) from the table; real chi(g) = +-1 enters as a sign bit
+                    R c;
+                    if constexpr (K == 0) {
+                        const double cd = jhs[jcls[tt] * G1 + nst];
+                        c = __longlong_as_double(__double_as_longlong(cd) ^ ((long long)t.chi_neg[g] << 63));
+                    } else {
+                        c = (R)flips[tt].jhalf * t.chif[g].x * t.sqrtnf[nst];
+                    }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        if (v < nvec) accr[v] += c * x[(int64_t)v * D + jx];
+                } else {
+                    const FlipTerm ft = flips[tt];
+                    // h = jhalf + i sum_t k_t s^z_c (spin a down ? +1 : -1)
+                    double him = 0.0;
+                    if (ft.pc0 >= 0) him += ft.k0 * (((s >> ft.pc0) & 1) ? 0.5 : -0.5);
+                    if (ft.pc1 >= 0) him += ft.k1 * (((s >> ft.pc1) & 1) ? 0.5 : -0.5);
+                    if ((s >> ft.pa) & 1) him = -him;
+                    R cr, ci;
+                    if constexpr (K == 2) {
+                        const double2 ch = t.chi[g];
+                        const double sq = t.sqrtn[nst];
+                        // conj(h) chi = (jh - i him)(chr + i chi)
+                        cr = (ft.jhalf * ch.x + him * ch.y) * sq;
+                        ci = (ft.jhalf * ch.y - him * ch.x) * sq;
+                    } else {
+                        const float2 ch = t.chif[g];
+                        const float sq = t.sqrtnf[nst];
+                        const float jh = (float)ft.jhalf, hm = (float)him;
+                        cr = (jh * ch.x + hm * ch.y) * sq;
+                        ci = (jh * ch.y - hm * ch.x) * sq;
+                    }
+#pragma unroll
+                    for (int v = 0; v < NV; ++v)
+                        if (v < nvec) {
+                            const T xj = x[(int64_t)v * D + jx];
+                            accr[v] += cr * xj.x - ci * xj.y;
+                            acci[v] += cr * xj.y + ci * xj.x;
+                        }
+                }
+            }
+        }
+        // y_i = acc_i / sqrt(|Stab sigma_i|) + diag_i x_i
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v < nvec) {
+                const int64_t o = (int64_t)v * D + row;
+                if constexpr (!V::cplx) {
+                    const R inv = (K == 0) ? (R)t.isqrtn[stab_row] : (R)t.isqrtnf[stab_row];
+                    y[o] = accr[v] * inv + (R)diag * x[o];
+                } else {
+                    const R inv = (K == 2) ? (R)t.isqrtn[stab_row] : (R)t.isqrtnf[stab_row];
+                    const T xi = x[o];
+                    T out;
+                    out.x = accr[v] * inv + (R)diag * xi.x;
+                    out.y = acci[v] * inv + (R)diag * xi.y;
+                    y[o] = out;
+                }
+            }
+        }
+    }
+    cnt.gather += n_gather;
+    cnt.skip += n_skip;
+    cnt.miss += n_miss;
+    __syncthreads();  // shared memory is restaged by the next call
+}
+
+__device__ __forceinline__ void flush_counts(Counts c, unsigned long long* counters) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c.gather += __shfl_xor_sync(0xffffffffu, c.gather, o);
+        c.skip += __shfl_xor_sync(0xffffffffu, c.skip, o);
+        c.miss += __shfl_xor_sync(0xffffffffu, c.miss, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c.gather) atomicAdd(counters + 0, c.gather);
+        if (c.skip) atomicAdd(counters + 1, c.skip);
+        if (c.miss) atomicAdd(counters + 2, c.miss);
+    }
+}
+
+template <typename W, bool CH, int K, int NV, int NS>
+__global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2) hx_kernel(HxArgs a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    Counts c;
+    hx_body<W, CH, K, NV, NS>(a, smem, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, a.D,
+                              (int64_t)gridDim.x * blockDim.x, c);
+    flush_counts(c, a.counters);
+}
+
+// All sectors of a batch in one launch.  Rows of all sectors form one index
+// space (sector s owns [row_off[s], row_off[s+1])); block b takes the
+// contiguous range [b*chunk, (b+1)*chunk) and, for every sector that range
+// meets, stages that sector's tables and processes its rows in a
+// block-stride loop.  Vectors are concatenated: sector s's block of nvec
+// vectors starts at element nvec*row_off[s] of x and y.
+template <typename W, bool CH, int K, int NV, int NS>
+__global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2)
+    hx_batch_kernel(const HxArgs* __restrict__ desc, const int64_t* __restrict__ row_off, int n_sec, int64_t chunk,
+                    const void* x, void* y, int nvec, const int* __restrict__ x_step, int64_t x_step_elems,
+                    unsigned long long* counters) {
+    using T = typename Val<K>::T;
+    // optional device-side block index: x advances by x_step_elems per step
+    // (lets one captured launch serve every step of a block Lanczos run)
+    if (x_step) x = (const T*)x + (int64_t)(*x_step) * x_step_elems;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const int64_t total = row_off[n_sec];
+    const int64_t g0 = (int64_t)blockIdx.x * chunk;
+    const int64_t g1 = min(total, g0 + chunk);
+    Counts c;
+    if (g0 < g1) {
+        // first sector meeting [g0, g1)
+        int lo = 0, hi = n_sec - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_off[mid] <= g0) lo = mid;
+            else hi = mid - 1;
+        }
+        for (int sct = lo; sct < n_sec && row_off[sct] < g1; ++sct) {
+            HxArgs a = desc[sct];
+            a.nvec = nvec;
+            const int64_t off = row_off[sct];
+            a.x = (const T*)x + (int64_t)a.nvec * off;
+            a.y = (T*)y + (int64_t)a.nvec * off;
+            const int64_t b = max(g0, off) - off, e = min(g1, row_off[sct + 1]) - off;
+            hx_body<W, CH, K, NV, NS>(a, smem, b + threadIdx.x, e, (int64_t)blockDim.x, c);
+        }
+    }
+    flush_counts(c, counters);
+}
+
+
+template <typename W, bool CH, int K, int NV, int NS>
+static ed_status launch(const HxArgs& a, size_t smem, cudaStream_t s) {
+    auto k = hx_kernel<W, CH, K, NV, NS>;
+    static int cfg_smem = -1, cfg_grid = 0;  // per instantiation
+    if ((int)smem != cfg_smem) {
+        ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        int dev = 0, sms = 0, per_sm = 0;
+        ED_CUDA(cudaGetDevice(&dev));
+        ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, smem));
+        if (per_sm < 1) return fail(ED_ERR_TABLE_TOO_LARGE, "H.x shared memory (%zu bytes) exceeds the device limit", smem);
+        cfg_smem = (int)smem;
+        cfg_grid = sms * per_sm;
+    }
+    int64_t grid = std::min<int64_t>(cfg_grid, (a.D + BLOCK - 1) / BLOCK);
+    if (grid < 1) grid = 1;
+    k<<<(unsigned)grid, BLOCK, smem, s>>>(a);
+    ED_CUDA(cudaGetLastError());
+    return ED_OK;
+}
+
+template <typename W, bool CH, int K, int NV>
+static ed_status launch_ns(const HxArgs& a, size_t smem, int n_sub, bool ns_ok, cudaStream_t s) {
+    if (ns_ok) {
+        if (n_sub == 2) return launch<W, CH, K, NV, 2>(a, smem, s);
+        if (n_sub == 3) return launch<W, CH, K, NV, 3>(a, smem, s);
+        if (n_sub == 4) return launch<W, CH, K, NV, 4>(a, smem, s);
+    }
+    return launch<W, CH, K, NV, 0>(a, smem, s);
+}
+
+template <typename W, bool CH, int K>
+static ed_status launch_nv(const HxArgs& a, size_t smem, int n_sub, bool ns_ok, cudaStream_t s) {
+    return a.nvec == 1 ? launch_ns<W, CH, K, 1>(a, smem, n_sub, ns_ok, s)
+                       : launch_ns<W, CH, K, MAXV>(a, smem, n_sub, ns_ok, s);
+}
+
+template <typename W, bool CH, int K, int NV, int NS>
+static ed_status launch_batch(const BatchLaunch& L, cudaStream_t s) {
+    auto k = hx_batch_kernel<W, CH, K, NV, NS>;
+    ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
+    int per_sm = 0;
+    ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, L.smem));
+    if (per_sm < 1) return fail(ED_ERR_TABLE_TOO_LARGE, "batched H.x shared memory (%zu bytes) exceeds the limit", L.smem);
+    int dev = 0, sms = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t grid = std::max<int64_t>(1, (int64_t)sms * per_sm * std::max(1, L.waves));
+    const int64_t chunk = std::max<int64_t>(1, (L.total_rows + grid - 1) / grid);
+    const int64_t nblk = (L.total_rows + chunk - 1) / chunk;
+    k<<<(unsigned)nblk, BLOCK, L.smem, s>>>(L.desc, L.row_off, L.n_sec, chunk, L.x, L.y, L.nvec, L.x_step,
+                                               L.x_step_elems, L.counters);
+    ED_CUDA(cudaGetLastError());
+    return ED_OK;
+}
+
+template <typename W, bool CH, int K>
+static ed_status batch_nv(const BatchLaunch& L, cudaStream_t s) {
+    auto ns = [&](auto nvtag) -> ed_status {
+        constexpr int NV = decltype(nvtag)::value;
+        if (L.ns_ok) {
+            if (L.n_sub == 2) return launch_batch<W, CH, K, NV, 2>(L, s);
+            if (L.n_sub == 3) return launch_batch<W, CH, K, NV, 3>(L, s);
+            if (L.n_sub == 4) return launch_batch<W, CH, K, NV, 4>(L, s);
+        }
+        return launch_batch<W, CH, K, NV, 0>(L, s);
+    };
+    return L.nvec == 1 ? ns(std::integral_constant<int, 1>{}) : ns(std::integral_constant<int, MAXV>{});
+}
+
+// entry points of one value kind (defined by ed_apply_kind.cuh per TU)
+template <int K>
+ed_status apply_launch_kind(const HxArgs& a, size_t smem, int n_sub, bool ns_ok, bool w8, bool chunked, cudaStream_t s) {
+    if (w8) return chunked ? launch_nv<uint64_t, true, K>(a, smem, n_sub, ns_ok, s)
+                           : launch_nv<uint64_t, false, K>(a, smem, n_sub, ns_ok, s);
+    return chunked ? launch_nv<uint32_t, true, K>(a, smem, n_sub, ns_ok, s)
+                   : launch_nv<uint32_t, false, K>(a, smem, n_sub, ns_ok, s);
+}
+
+template <int K>
+ed_status apply_batch_kind(const BatchLaunch& L, cudaStream_t s) {
+    if (L.w8) return L.chunked ? batch_nv<uint64_t, true, K>(L, s) : batch_nv<uint64_t, false, K>(L, s);
+    return L.chunked ? batch_nv<uint32_t, true, K>(L, s) : batch_nv<uint32_t, false, K>(L, s);
+}
+
+}  // namespace ed

@@ -1,0 +1,7 @@
+// H.x kernels for value kind 0 (FP64 vectors).
+#include "ed_apply_impl.cuh"
+
+namespace ed {
+template ed_status apply_launch_kind<0>(const HxArgs&, size_t, int, bool, bool, bool, cudaStream_t);
+template ed_status apply_batch_kind<0>(const BatchLaunch&, cudaStream_t);
+}  // namespace ed

@@ -1,0 +1,731 @@
+// Batches of sectors: one H.x launch over all sectors, and block Lanczos
+// (several right-hand sides per sector) for all sectors at once.
+//
+// Vector layout of a batch: sectors are concatenated in order; sector s owns
+// rows [row_off[s], row_off[s+1]) and its block of b vectors starts at
+// element b*row_off[s], column-major (column c at b*row_off[s] + c*D_s).
+//
+// Block Lanczos (the block form of the Lanczos recursion, Eqs.
+// lanczosrecursionabbrev and tmatrix with b x b blocks): for block k,
+// W = H V_k; classical Gram-Schmidt twice against every stored block V_j
+// (j <= k), which also yields the diagonal block A_k = V_k^H H V_k; then
+// W = V_{k+1} B_k by Cholesky QR applied twice.  All inner products accumulate
+// in FP64 over fixed row tiles and are reduced in a fixed order.  Every kernel
+// of a step takes the block index from device memory, so the whole step is
+// captured once as a CUDA graph and replayed; the host only reads the small
+// blocks A_k, B_k and solves the banded T-matrix for eigenvalues by bisection
+// on Sturm (inertia) counts of its banded LDL^H factorisation.
+#include <math.h>
+
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <vector>
+
+#include "ed_internal.h"
+
+struct ed_batch {
+    std::vector<const ed_hamiltonian*> hs;
+    std::vector<int64_t> row_off;          // host [n+1]
+    ed::DevBuf d_desc, d_row_off, d_counters, d_tiles;
+    int n = 0;
+    int64_t total = 0;
+    size_t smem = 0;
+    bool w8 = false, chunked = false, ns_ok = false, all_real = true;
+    int n_sub = 0;
+    int waves[4][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}};  // [dtype][nvec>1]: tuned grid waves
+    std::vector<int64_t> tiles;            // row tiles: (sector, begin, end) triples
+    int n_tiles = 0;
+    const ed::Alloc* alloc = nullptr;
+};
+
+namespace ed {
+
+static const int TILE = 4096;  // rows per reduction tile
+static const int MAXB = 8;
+
+template <int K> struct BV;
+template <> struct BV<0> { using T = double; static constexpr bool cplx = false; };
+template <> struct BV<2> { using T = double2; static constexpr bool cplx = true; };
+
+__device__ __forceinline__ double2 c_ld(const double& v) { return make_double2(v, 0.0); }
+__device__ __forceinline__ double2 c_ld(const double2& v) { return v; }
+__device__ __forceinline__ void c_st(double& d, double2 v) { d = v.x; }
+__device__ __forceinline__ void c_st(double2& d, double2 v) { d = v; }
+__device__ __forceinline__ double2 c_mul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ double2 c_conjmul(double2 a, double2 b) {  // conj(a) b
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+
+__device__ __forceinline__ int sector_of(const int64_t* row_off, int n, int64_t r) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (row_off[mid] <= r) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint64_t bmix(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+__device__ __forceinline__ double bunif(uint64_t seed, uint64_t stream, uint64_t state) {
+    const uint64_t key = bmix(seed * 256ull + stream);
+    return ((double)(bmix(state ^ key) >> 11) + 0.5) * (1.0 / 9007199254740992.0);  // (0,1)
+}
+
+// Start block: Gaussian entries (Box-Muller on keyed SplitMix64 uniforms of
+// the state integer, one stream pair per column and component).
+template <int K>
+__global__ void bl_init(typename BV<K>::T* X, const HxArgs* desc, const int64_t* row_off, int n, int b, uint64_t seed,
+                        int word) {
+    const int64_t total = row_off[n];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sector_of(row_off, n, r);
+        const int64_t i = r - row_off[s];
+        const int64_t D = row_off[s + 1] - row_off[s];
+        const uint64_t st = word == 8 ? ((const uint64_t*)desc[s].reps)[i] : ((const uint32_t*)desc[s].reps)[i];
+        for (int c = 0; c < b; ++c) {
+            const double u1 = bunif(seed, 4 * c, st), u2 = bunif(seed, 4 * c + 1, st);
+            const double rr = sqrt(-2.0 * log(u1));
+            double2 z = make_double2(rr * cos(6.283185307179586 * u2), 0.0);
+            if (BV<K>::cplx) {
+                const double u3 = bunif(seed, 4 * c + 2, st), u4 = bunif(seed, 4 * c + 3, st);
+                z.y = sqrt(-2.0 * log(u3)) * cos(6.283185307179586 * u4);
+            }
+            c_st(X[b * row_off[s] + (int64_t)c * D + i], z);
+        }
+    }
+}
+
+// partial[j][tile][a][c] = sum over tile rows of conj(X_j[a][i]) Y[c][i],
+// X_j = X + j*xs (j = 0..*jmax, or 0 when jmax is null).  One block per
+// (tile, j); thread t handles pair (a, c) = (t / b % b, t % b) for rows
+// i = t / b^2 + m * (256 / b^2).
+template <int K>
+__global__ void __launch_bounds__(256) bl_gram(const typename BV<K>::T* X, int64_t xs, const int* jmax,
+                                               const typename BV<K>::T* Y, const int64_t* tiles,
+                                               const int64_t* row_off, int b, double2* partial, int n_tiles) {
+    const int j = blockIdx.y;
+    if (jmax ? j > *jmax : j > 0) return;
+    const int tile = blockIdx.x;
+    const int s = (int)tiles[3 * tile];
+    const int64_t i0 = tiles[3 * tile + 1], i1 = tiles[3 * tile + 2];
+    const int64_t D = row_off[s + 1] - row_off[s];
+    const int64_t base = (int64_t)b * row_off[s];
+    const int bb = b * b;
+    const int lanes = 256 / bb;
+    const int t = threadIdx.x;
+    __shared__ double2 red[256];
+    double2 acc = make_double2(0.0, 0.0);
+    if (t < lanes * bb) {
+        const int a = (t / b) % b, c = t % b, l = t / bb;
+        const typename BV<K>::T* xa = X + (int64_t)j * xs + base + (int64_t)a * D;
+        const typename BV<K>::T* yc = Y + base + (int64_t)c * D;
+        for (int64_t i = i0 + l; i < i1; i += lanes) {
+            const double2 p = c_conjmul(c_ld(xa[i]), c_ld(yc[i]));
+            acc.x += p.x;
+            acc.y += p.y;
+        }
+    }
+    red[t] = acc;
+    __syncthreads();
+    if (t < bb) {
+        double2 sum = make_double2(0.0, 0.0);
+        for (int l = 0; l < lanes; ++l) {
+            sum.x += red[l * bb + t].x;
+            sum.y += red[l * bb + t].y;
+        }
+        partial[((int64_t)j * n_tiles + tile) * bb + t] = sum;
+    }
+}
+
+// C[s][j][a][c] = sum over the tiles of sector s (fixed order)
+__global__ void bl_reduce(const double2* partial, const int* tile_first, int n, int b, int n_tiles, const int* jmax,
+                          int jcap, double2* C) {
+    const int s = blockIdx.x;
+    const int bb = b * b;
+    const int jm = jmax ? *jmax : 0;
+    for (int e = threadIdx.x; e < (jm + 1) * bb; e += blockDim.x) {
+        const int j = e / bb, ac = e % bb;
+        double2 sum = make_double2(0.0, 0.0);
+        for (int tl = tile_first[s]; tl < tile_first[s + 1]; ++tl) {
+            const double2 v = partial[((int64_t)j * n_tiles + tl) * bb + ac];
+            sum.x += v.x;
+            sum.y += v.y;
+        }
+        C[((int64_t)s * jcap + j) * bb + ac] = sum;
+    }
+}
+
+// W[c][i] -= sum_{j <= jmax} sum_a X_j[a][i] C[s][j][a][c]
+template <int K>
+__global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int64_t xs, const int* jmax,
+                          const double2* C, int jcap, const int64_t* row_off, int n, int b) {
+    const int64_t total = row_off[n];
+    const int jm = *jmax;
+    const int bb = b * b;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sector_of(row_off, n, r);
+        const int64_t i = r - row_off[s];
+        const int64_t D = row_off[s + 1] - row_off[s];
+        const int64_t base = (int64_t)b * row_off[s];
+        double2 w[MAXB];
+        for (int c = 0; c < b; ++c) w[c] = c_ld(W[base + (int64_t)c * D + i]);
+        for (int j = 0; j <= jm; ++j) {
+            const double2* Cj = C + ((int64_t)s * jcap + j) * bb;
+            for (int a = 0; a < b; ++a) {
+                const double2 x = c_ld(X[(int64_t)j * xs + base + (int64_t)a * D + i]);
+                for (int c = 0; c < b; ++c) {
+                    const double2 p = c_mul(x, Cj[a * b + c]);
+                    w[c].x -= p.x;
+                    w[c].y -= p.y;
+                }
+            }
+        }
+        for (int c = 0; c < b; ++c) c_st(W[base + (int64_t)c * D + i], w[c]);
+    }
+}
+
+// Per sector: G = R^H R (Cholesky, G from the W^H W gram), store R^{-1} and
+// accumulate Bacc = R * Bacc (Bacc starts as the identity).  A column whose
+// pivot collapses is dropped (R^{-1} column zero).
+__global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv, double2* Bacc, int first_pass) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    const int bb = b * b;
+    const double2* g = G + (int64_t)s * jcap * bb;  // j = 0 slot
+    double2 R[MAXB][MAXB], Ri[MAXB][MAXB];
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) { R[r][c] = make_double2(0, 0); Ri[r][c] = make_double2(0, 0); }
+    double scale = 0.0;
+    for (int a = 0; a < b; ++a) scale = fmax(scale, g[a * b + a].x);
+    for (int c = 0; c < b; ++c) {
+        // R[r][c] for r < c, then R[c][c]
+        for (int r = 0; r < c; ++r) {
+            // G[r][c] = sum_{k<=r} conj(R[k][r]) R[k][c]
+            double2 v = g[r * b + c];
+            for (int k = 0; k < r; ++k) {
+                const double2 p = c_conjmul(R[k][r], R[k][c]);
+                v.x -= p.x;
+                v.y -= p.y;
+            }
+            const double d = R[r][r].x;
+            R[r][c] = d > 0 ? make_double2(v.x / d, v.y / d) : make_double2(0, 0);
+        }
+        double v = g[c * b + c].x;
+        for (int k = 0; k < c; ++k) v -= R[k][c].x * R[k][c].x + R[k][c].y * R[k][c].y;
+        R[c][c] = make_double2(v > 1e-28 * scale ? sqrt(v) : 0.0, 0.0);
+    }
+    // inverse of the upper-triangular R (zero rows/columns for dropped pivots)
+    for (int c = 0; c < b; ++c) {
+        if (R[c][c].x <= 0) continue;
+        Ri[c][c] = make_double2(1.0 / R[c][c].x, 0.0);
+        for (int r = c - 1; r >= 0; --r) {
+            if (R[r][r].x <= 0) continue;
+            double2 v = make_double2(0, 0);
+            for (int k = r + 1; k <= c; ++k) {
+                const double2 p = c_mul(R[r][k], Ri[k][c]);
+                v.x += p.x;
+                v.y += p.y;
+            }
+            Ri[r][c] = make_double2(-v.x / R[r][r].x, -v.y / R[r][r].x);
+        }
+    }
+    double2* ri = Rinv + (int64_t)s * bb;
+    double2* ba = Bacc + (int64_t)s * bb;
+    double2 Bn[MAXB][MAXB];
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) {
+            ri[r * b + c] = Ri[r][c];
+            double2 v = make_double2(0, 0);
+            for (int k = 0; k < b; ++k) {
+                const double2 prev = first_pass ? make_double2(k == c ? 1.0 : 0.0, 0.0) : ba[k * b + c];
+                const double2 p = c_mul(R[r][k], prev);
+                v.x += p.x;
+                v.y += p.y;
+            }
+            Bn[r][c] = v;
+        }
+    for (int r = 0; r < b; ++r)
+        for (int c = 0; c < b; ++c) ba[r * b + c] = Bn[r][c];
+}
+
+// Out[c][i] = sum_a W[a][i] Rinv[s][a][c]; Out may be W + (*kout)*os (device index) or W itself
+template <int K>
+__global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int64_t os, const int* kout, int kadd,
+                         const double2* Rinv, const int64_t* row_off, int n, int b) {
+    const int64_t total = row_off[n];
+    typename BV<K>::T* out = Out + (kout ? (int64_t)(*kout + kadd) * os : 0);
+    const int bb = b * b;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sector_of(row_off, n, r);
+        const int64_t i = r - row_off[s];
+        const int64_t D = row_off[s + 1] - row_off[s];
+        const int64_t base = (int64_t)b * row_off[s];
+        double2 w[MAXB];
+        for (int a = 0; a < b; ++a) w[a] = c_ld(W[base + (int64_t)a * D + i]);
+        const double2* R = Rinv + (int64_t)s * bb;
+        for (int c = 0; c < b; ++c) {
+            double2 v = make_double2(0, 0);
+            for (int a = 0; a < b; ++a) {
+                const double2 p = c_mul(w[a], R[a * b + c]);
+                v.x += p.x;
+                v.y += p.y;
+            }
+            c_st(out[base + (int64_t)c * D + i], v);
+        }
+    }
+}
+
+// Save A_k (= the j = k block of the first and second reorthogonalisation
+// coefficients, summed) and B_k (Bacc) into the per-step arrays; advance k.
+__global__ void bl_save(const double2* C1, const double2* C2, const double2* Bacc, int jcap, int n, int b, int* k,
+                        double2* Ahist, double2* Bhist, int kcap) {
+    const int kk = *k;
+    const int bb = b * b;
+    for (int e = threadIdx.x; e < n * bb; e += blockDim.x) {
+        const int s = e / bb, ac = e % bb;
+        const double2 a1 = C1[((int64_t)s * jcap + kk) * bb + ac], a2 = C2[((int64_t)s * jcap + kk) * bb + ac];
+        Ahist[((int64_t)s * kcap + kk) * bb + ac] = make_double2(a1.x + a2.x, a1.y + a2.y);
+        Bhist[((int64_t)s * kcap + kk) * bb + ac] = Bacc[(int64_t)s * bb + ac];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) *k = kk + 1;
+}
+
+__global__ void bl_set_int(int* p, int v) { *p = v; }
+
+// ------------------------------------------------------------------ host: banded eigenvalues
+using cd = std::complex<double>;
+
+// number of eigenvalues of the Hermitian band matrix T (n x n, bandwidth bw,
+// dense storage) below x: negative pivots of the banded LDL^H of T - x I
+static int band_count(const std::vector<cd>& T, int n, int bw, double x) {
+    std::vector<cd> L((size_t)n * (bw + 1), cd(0));  // L[i][i-k] at i*(bw+1)+k
+    std::vector<double> d(n, 0.0);
+    int neg = 0;
+    for (int j = 0; j < n; ++j) {
+        double dj = T[(size_t)j * n + j].real() - x;
+        for (int k = std::max(0, j - bw); k < j; ++k) dj -= std::norm(L[(size_t)j * (bw + 1) + (j - k)]) * d[k];
+        if (dj == 0.0) dj = 1e-300;
+        d[j] = dj;
+        if (dj < 0) ++neg;
+        for (int i = j + 1; i <= std::min(n - 1, j + bw); ++i) {
+            cd v = T[(size_t)i * n + j];
+            for (int k = std::max(0, i - bw); k < j; ++k)
+                v -= L[(size_t)i * (bw + 1) + (i - k)] * std::conj(L[(size_t)j * (bw + 1) + (j - k)]) * d[k];
+            L[(size_t)i * (bw + 1) + (i - j)] = v / dj;
+        }
+    }
+    return neg;
+}
+
+static std::vector<double> band_lowest(const std::vector<cd>& T, int n, int bw, int k) {
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+        double r = 0;
+        for (int j = 0; j < n; ++j)
+            if (j != i) r += std::abs(T[(size_t)i * n + j]);
+        lo = std::min(lo, T[(size_t)i * n + i].real() - r);
+        hi = std::max(hi, T[(size_t)i * n + i].real() + r);
+    }
+    std::vector<double> out;
+    for (int e = 0; e < std::min(k, n); ++e) {
+        double a = lo, b2 = hi;
+        for (int it = 0; it < 200; ++it) {
+            const double m = 0.5 * (a + b2);
+            if (m <= a || m >= b2) break;
+            if (band_count(T, n, bw, m) > e) b2 = m;
+            else a = m;
+        }
+        out.push_back(0.5 * (a + b2));
+    }
+    return out;
+}
+
+// ------------------------------------------------------------------ batch construction and apply
+static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n) {
+    if (!hs || n < 1) return fail(ED_ERR_ARG, "empty batch");
+    B->hs.assign(hs, hs + n);
+    B->n = n;
+    const ed_basis* b0 = hs[0]->basis;
+    B->alloc = &b0->alloc;
+    B->w8 = b0->word == 8;
+    B->chunked = b0->dt.chunk_lo > 0;
+    B->n_sub = b0->ht.n_sub;
+    B->ns_ok = true;
+    B->row_off.assign(n + 1, 0);
+    std::vector<HxArgs> desc(n);
+    B->all_real = true;
+    for (int s = 0; s < n; ++s) {
+        const ed_hamiltonian* h = hs[s];
+        if (!h) return fail(ED_ERR_ARG, "null Hamiltonian %d", s);
+        const ed_basis* b = h->basis;
+        if ((b->word == 8) != B->w8 || (b->dt.chunk_lo > 0) != B->chunked || b->ht.n_sub != B->n_sub ||
+            b->ht.m != b0->ht.m)
+            return fail(ED_ERR_ARG, "sector %d has a different state word or block structure", s);
+        if (h->n_flip > 256) return fail(ED_ERR_ARG, "more than 256 flip terms");
+        B->ns_ok = B->ns_ok && b->dt.dl_stride == 4;
+        B->all_real = B->all_real && h->is_real;
+        desc[s] = make_args(h);
+        B->row_off[s + 1] = B->row_off[s] + b->dim;
+        B->smem = std::max(B->smem, hx_smem_bytes(h));
+    }
+    B->total = B->row_off[n];
+    // reduction tiles: (sector, begin, end), TILE rows, never crossing sectors
+    B->tiles.clear();
+    for (int s = 0; s < n; ++s)
+        for (int64_t i = 0; i < B->row_off[s + 1] - B->row_off[s]; i += TILE)
+            B->tiles.insert(B->tiles.end(),
+                            {(int64_t)s, i, std::min<int64_t>(i + TILE, B->row_off[s + 1] - B->row_off[s])});
+    B->n_tiles = (int)(B->tiles.size() / 3);
+    const Alloc& A = *B->alloc;
+    auto up = [&](DevBuf& d, const void* src, size_t bytes) -> bool {
+        d.bytes = bytes ? bytes : 16;
+        d.p = A.get(d.bytes, 0);
+        return d.p && (!bytes || cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess);
+    };
+    if (!up(B->d_desc, desc.data(), desc.size() * sizeof(HxArgs)) ||
+        !up(B->d_row_off, B->row_off.data(), B->row_off.size() * 8) ||
+        !up(B->d_tiles, B->tiles.data(), B->tiles.size() * 8))
+        return fail(ED_ERR_NOMEM, "batch descriptors");
+    B->d_counters.bytes = 32;
+    B->d_counters.p = A.get(32, 0);
+    if (!B->d_counters.p) return fail(ED_ERR_NOMEM, "batch counters");
+    ED_CUDA(cudaMemset(B->d_counters.p, 0, 32));
+    return ED_OK;
+}
+
+static int dkind(ed_dtype d) { return d == ED_F64 ? 0 : d == ED_F32 ? 1 : d == ED_C128 ? 2 : 3; }
+
+static BatchLaunch make_launch(const ed_batch* B, ed_dtype dt, const void* x, void* y, int nvec) {
+    BatchLaunch L{};
+    L.desc = (const HxArgs*)B->d_desc.p;
+    L.row_off = (const int64_t*)B->d_row_off.p;
+    L.n_sec = B->n;
+    L.total_rows = B->total;
+    L.smem = B->smem;
+    L.w8 = B->w8;
+    L.chunked = B->chunked;
+    L.ns_ok = B->ns_ok;
+    L.n_sub = B->n_sub;
+    L.dtype = dt;
+    L.nvec = nvec;
+    L.x = x;
+    L.y = y;
+    L.counters = (unsigned long long*)B->d_counters.p;
+    L.waves = B->waves[dkind(dt)][nvec > 1 ? 1 : 0];
+    return L;
+}
+
+}  // namespace ed
+
+using namespace ed;
+
+extern "C" {
+
+ed_status ed_batch_create(const ed_hamiltonian* const* h, int32_t n, ed_batch** out) {
+    if (!out) return fail(ED_ERR_ARG, "out is null");
+    *out = nullptr;
+    ed_batch* B = new ed_batch();
+    ed_status st = batch_init(B, h, n);
+    if (st != ED_OK) {
+        ed_batch_free(B);
+        return st;
+    }
+    *out = B;
+    return ED_OK;
+}
+
+ed_status ed_batch_rows(const ed_batch* B, int64_t* row_off) {
+    if (!B || !row_off) return fail(ED_ERR_ARG, "null argument");
+    for (int s = 0; s <= B->n; ++s) row_off[s] = B->row_off[s];
+    return ED_OK;
+}
+
+ed_status ed_apply_batch(const ed_batch* B, ed_dtype dtype, const void* x, void* y, int32_t nvec, ed_stream stream) {
+    if (!B || !x || !y) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > 8) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    if ((dtype == ED_F64 || dtype == ED_F32) && !B->all_real)
+        return fail(ED_ERR_ARG, "a complex sector needs a complex dtype");
+    BatchLaunch L = make_launch(B, dtype, x, y, nvec);
+    ED_CUDA(cudaMemsetAsync(B->d_counters.p, 0, 24, (cudaStream_t)stream));
+    return apply_batch_launch(L, (cudaStream_t)stream);
+}
+
+ed_status ed_batch_autotune(ed_batch* B, ed_dtype dtype, const void* x, void* y, int32_t nvec, ed_stream stream,
+                            int32_t* waves_out) {
+    if (!B || !x || !y) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > 8) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaEvent_t e0, e1;
+    ED_CUDA(cudaEventCreate(&e0));
+    ED_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_w = 1;
+    for (int w : {1, 2, 4, 8, 16}) {
+        BatchLaunch L = make_launch(B, dtype, x, y, nvec);
+        L.waves = w;
+        ed_status st = apply_batch_launch(L, s);  // warm-up
+        if (st != ED_OK) return st;
+        ED_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 3; ++r) {
+            st = apply_batch_launch(L, s);
+            if (st != ED_OK) return st;
+        }
+        ED_CUDA(cudaEventRecord(e1, s));
+        ED_CUDA(cudaEventSynchronize(e1));
+        float ms = 0;
+        ED_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; best_w = w; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    B->waves[dkind(dtype)][nvec > 1 ? 1 : 0] = best_w;
+    if (waves_out) *waves_out = best_w;
+    return ED_OK;
+}
+
+void ed_batch_free(ed_batch* B) {
+    if (!B) return;
+    if (B->alloc) {
+        B->alloc->put(B->d_desc.p, B->d_desc.bytes, 0);
+        B->alloc->put(B->d_row_off.p, B->d_row_off.bytes, 0);
+        B->alloc->put(B->d_tiles.p, B->d_tiles.bytes, 0);
+        B->alloc->put(B->d_counters.p, B->d_counters.bytes, 0);
+    }
+    delete B;
+}
+
+}  // extern "C"
+
+namespace ed {
+
+template <int K>
+static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o, double* evals,
+                               ed_block_lanczos_report* rep, cudaStream_t user_stream) {
+    using T = typename BV<K>::T;
+    auto t0 = std::chrono::steady_clock::now();
+    const int n = B->n, b = o->block, kcap = o->max_iter + 1, nt = B->n_tiles;
+    const int64_t tot = B->total;
+    const int64_t bs = (int64_t)b * tot;  // elements per block vector
+    const Alloc& A = *B->alloc;
+    std::vector<std::pair<void*, size_t>> bufs;
+    auto get = [&](size_t bytes) {
+        void* p = A.get(bytes, 0);
+        if (p) bufs.push_back({p, bytes});
+        return p;
+    };
+    struct Free {
+        std::vector<std::pair<void*, size_t>>& v;
+        const Alloc& A;
+        ~Free() {
+            cudaDeviceSynchronize();
+            for (auto& p : v) A.put(p.first, p.second, 0);
+        }
+    } freer{bufs, A};
+    const int bb = b * b;
+    T* V = (T*)get((size_t)kcap * bs * sizeof(T));
+    T* W = (T*)get((size_t)bs * sizeof(T));
+    double2* part = (double2*)get((size_t)kcap * nt * bb * sizeof(double2));
+    double2* C1 = (double2*)get((size_t)n * kcap * bb * sizeof(double2));
+    double2* C2 = (double2*)get((size_t)n * kcap * bb * sizeof(double2));
+    double2* G = (double2*)get((size_t)n * kcap * bb * sizeof(double2));
+    double2* Rinv = (double2*)get((size_t)n * bb * sizeof(double2));
+    double2* Bacc = (double2*)get((size_t)n * bb * sizeof(double2));
+    double2* Ahist = (double2*)get((size_t)n * kcap * bb * sizeof(double2));
+    double2* Bhist = (double2*)get((size_t)n * kcap * bb * sizeof(double2));
+    int* dk = (int*)get(16);
+    int* tile_first = (int*)get((size_t)(n + 1) * 4);
+    if (!V || !W || !part || !C1 || !C2 || !G || !Rinv || !Bacc || !Ahist || !Bhist || !dk || !tile_first)
+        return fail(ED_ERR_NOMEM, "block Lanczos workspace");
+    {
+        std::vector<int> tf(n + 1, 0);
+        for (int t = 0, s = 0; s <= n; ++s) {
+            while (t < nt && B->tiles[3 * t] < s) ++t;
+            tf[s] = t;
+        }
+        tf[n] = nt;
+        ED_CUDA(cudaMemcpy(tile_first, tf.data(), (n + 1) * 4, cudaMemcpyHostToDevice));
+    }
+    cudaStream_t s;
+    ED_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    struct SFree {
+        cudaStream_t s;
+        ~SFree() { cudaStreamDestroy(s); }
+    } sfree{s};
+    (void)user_stream;
+    int sms = 0, dev = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned g = (unsigned)std::min<int64_t>((tot + 255) / 256, (int64_t)sms * 8);
+    const int64_t* ro = (const int64_t*)B->d_row_off.p;
+    const int64_t* tiles = (const int64_t*)B->d_tiles.p;
+    const HxArgs* desc = (const HxArgs*)B->d_desc.p;
+    // start block V_0 = orth(X), via CholQR2 on the Gaussian block
+    bl_init<K><<<g, 256, 0, s>>>(W, desc, ro, n, b, o->seed, B->w8 ? 8 : 4);
+    auto cholqr = [&](T* src, T* dst, int64_t dst_os, const int* kout, int kadd) {
+        for (int pass = 0; pass < 2; ++pass) {
+            bl_gram<K><<<dim3(nt, 1), 256, 0, s>>>(src, 0, nullptr, src, tiles, ro, b, part, nt);
+            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, nullptr, kcap, G);
+            bl_chol<<<(n + 63) / 64, 64, 0, s>>>(G, kcap, n, b, Rinv, Bacc, pass == 0);
+            bl_scale<K><<<g, 256, 0, s>>>(src, pass == 0 ? src : dst, dst_os, pass == 0 ? nullptr : kout, kadd, Rinv,
+                                          ro, n, b);
+        }
+    };
+    bl_set_int<<<1, 1, 0, s>>>(dk, 0);
+    cholqr(W, V, bs, dk, 0);  // V_0
+    ED_CUDA(cudaGetLastError());
+    // one step, all sectors
+    BatchLaunch L = make_launch(B, o->dtype, V, W, b);
+    L.x_step = dk;
+    L.x_step_elems = bs;
+    auto step = [&]() -> ed_status {
+        ed_status st = apply_batch_launch(L, s);  // W = H V_k
+        if (st != ED_OK) return st;
+        for (int pass = 0; pass < 2; ++pass) {
+            double2* Cp = pass == 0 ? C1 : C2;
+            bl_gram<K><<<dim3(nt, kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt);
+            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp);
+            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b);
+        }
+        cholqr(W, V, bs, dk, 1);  // V_{k+1} = W R^-1, B_k accumulated in Bacc
+        bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap);
+        return ED_OK;
+    };
+    // load every kernel of the step once outside any capture; the values this
+    // writes (W, C1, the step-0 history) are recomputed by the first step
+    {
+        ed_status st = apply_batch_launch(L, s);
+        if (st != ED_OK) return st;
+        bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b);
+        bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap);
+        bl_set_int<<<1, 1, 0, s>>>(dk, 0);
+        ED_CUDA(cudaGetLastError());
+        ED_CUDA(cudaStreamSynchronize(s));
+    }
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    if (o->use_graph) {
+        ED_CUDA(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+        ed_status st = step();
+        cudaGraph_t gr = nullptr;
+        cudaError_t ce = cudaStreamEndCapture(s, &gr);
+        if (st != ED_OK) return st;
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        graph = gr;
+        ED_CUDA(cudaGraphInstantiate(&gexec, graph, 0));
+    }
+    struct GFree {
+        cudaGraphExec_t e;
+        cudaGraph_t g;
+        ~GFree() {
+            if (e) cudaGraphExecDestroy(e);
+            if (g) cudaGraphDestroy(g);
+        }
+    } gfree{gexec, graph};
+    const int n_eig = o->n_eig;
+    std::vector<std::vector<double>> prev(n, std::vector<double>(n_eig, 1e300)), cur = prev;
+    std::vector<int> steady(n, 0);
+    std::vector<double2> Ah((size_t)n * kcap * bb), Bh((size_t)n * kcap * bb);
+    int iters = 0, conv_all = 0;
+    double t_steps = 0;
+    const int every = std::max(1, o->check_every);
+    for (int k = 0; k + 1 < kcap; ++k) {
+        auto ts = std::chrono::steady_clock::now();
+        if (gexec) ED_CUDA(cudaGraphLaunch(gexec, s));
+        else {
+            ed_status st = step();
+            if (st != ED_OK) return st;
+        }
+        ED_CUDA(cudaStreamSynchronize(s));
+        t_steps += std::chrono::duration<double>(std::chrono::steady_clock::now() - ts).count();
+        iters = k + 1;
+        const bool last = k + 2 >= kcap;
+        if ((k + 1) % every && !last) continue;
+        ED_CUDA(cudaMemcpy(Ah.data(), Ahist, Ah.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+        ED_CUDA(cudaMemcpy(Bh.data(), Bhist, Bh.size() * sizeof(double2), cudaMemcpyDeviceToHost));
+        // T (iters*b square): diag blocks A_j, block (j+1, j) = B_j.  Columns of
+        // V_{j+1} that collapsed in the Cholesky QR (zero diagonal of B_j, a
+        // sector smaller than the Krylov space) are left out of T.
+        const int nt2 = iters * b;
+        int nconv = 0;
+        for (int sct = 0; sct < n; ++sct) {
+            std::vector<cd> Tf((size_t)nt2 * nt2, cd(0));
+            std::vector<char> valid(nt2, 1);
+            double tn = 0.0;
+            for (int j = 0; j < iters; ++j) {
+                const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
+                for (int r = 0; r < b; ++r)
+                    for (int c = 0; c < b; ++c) {
+                        // Hermitian part of A_j
+                        const cd v = 0.5 * (cd(Aj[r * b + c].x, Aj[r * b + c].y) + std::conj(cd(Aj[c * b + r].x, Aj[c * b + r].y)));
+                        Tf[(size_t)(j * b + r) * nt2 + j * b + c] = v;
+                        tn = std::max(tn, std::abs(v));
+                    }
+                if (j + 1 < iters) {
+                    const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
+                    for (int r = 0; r < b; ++r) {
+                        if (!(Bj[r * b + r].x > 1e-12 * std::max(tn, 1e-300))) valid[(j + 1) * b + r] = 0;
+                        for (int c = 0; c < b; ++c) {
+                            const cd v(Bj[r * b + c].x, Bj[r * b + c].y);
+                            Tf[(size_t)((j + 1) * b + r) * nt2 + j * b + c] = v;
+                            Tf[(size_t)(j * b + c) * nt2 + (j + 1) * b + r] = std::conj(v);
+                        }
+                    }
+                }
+            }
+            std::vector<int> keep;
+            for (int i = 0; i < nt2; ++i)
+                if (valid[i]) keep.push_back(i);
+            const int nk2 = (int)keep.size();
+            std::vector<cd> Tm((size_t)nk2 * nk2);
+            for (int r = 0; r < nk2; ++r)
+                for (int c = 0; c < nk2; ++c) Tm[(size_t)r * nk2 + c] = Tf[(size_t)keep[r] * nt2 + keep[c]];
+            std::vector<double> lam = band_lowest(Tm, nk2, 2 * b - 1, n_eig);
+            bool ok = (int)lam.size() == n_eig;
+            for (int e = 0; e < (int)lam.size(); ++e) {
+                cur[sct][e] = lam[e];
+                const double sc = std::max(1.0, fabs(lam[e]));
+                if (fabs(lam[e] - prev[sct][e]) > o->tol * sc) ok = false;
+            }
+            steady[sct] = ok ? steady[sct] + 1 : 0;
+            if (steady[sct] >= 2) ++nconv;
+            prev[sct] = cur[sct];
+        }
+        conv_all = nconv;
+        if (nconv == n || last) break;
+    }
+    for (int sct = 0; sct < n; ++sct)
+        for (int e = 0; e < n_eig; ++e) evals[(size_t)sct * n_eig + e] = cur[sct][e];
+    if (rep) {
+        rep->iters = iters;
+        rep->converged_sectors = conv_all;
+        rep->krylov_dim = iters * b;
+        rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        rep->step_seconds = t_steps;
+        rep->used_graph = gexec ? 1 : 0;
+    }
+    return conv_all == n ? ED_OK : fail(ED_ERR_NOT_CONVERGED, "%d of %d sectors converged", conv_all, n);
+}
+
+}  // namespace ed
+
+extern "C" ed_status ed_lanczos_batch(const ed_batch* B, const ed_block_lanczos_opts* o, double* evals,
+                                      ed_block_lanczos_report* rep, ed_stream stream) {
+    if (!B || !o || !evals) return fail(ED_ERR_ARG, "null argument");
+    if (o->block < 1 || o->block > 8) return fail(ED_ERR_ARG, "block size out of range [1,8]");
+    if (o->n_eig < 1 || o->n_eig > 64) return fail(ED_ERR_ARG, "n_eig out of range");
+    if (o->max_iter < 2 || o->max_iter > 400) return fail(ED_ERR_ARG, "max_iter out of range [2,400]");
+    if (o->dtype == ED_F64) {
+        if (!B->all_real) return fail(ED_ERR_ARG, "a complex sector needs ED_C128");
+        return block_lanczos<0>(B, o, evals, rep, (cudaStream_t)stream);
+    }
+    if (o->dtype == ED_C128) return block_lanczos<2>(B, o, evals, rep, (cudaStream_t)stream);
+    return fail(ED_ERR_ARG, "block Lanczos supports ED_F64 and ED_C128");
+}

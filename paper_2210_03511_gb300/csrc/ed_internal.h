@@ -149,6 +149,50 @@ struct ed_hamiltonian {
 };
 
 namespace ed {
+// Arguments of one sector's H.x (device pointers; see ed_apply.cu).
+struct HxArgs {
+    DevTables dt;
+    const void* reps;
+    const uint16_t* stab;
+    const uint32_t* dir_base;
+    const uint8_t* dir_q;
+    const uint32_t* limits;
+    int L, S;
+    const FlipTerm* flips;
+    int n_flip;
+    const int8_t* diag_pos;       // [2*n_diag_bonds] bit positions, bonds sorted by class
+    const DiagClass* diag_cls;
+    int n_diag_cls, n_diag_bonds;
+    const double* jhs;            // [n_jc][G+1] jhalf_c * sqrt(n) for real kinds (class c of each term)
+    const uint8_t* jcls;          // [n_flip] class of each flip term
+    int n_jc;
+    const void* x;
+    void* y;
+    int nvec;
+    int64_t D;
+    unsigned long long* counters;  // [0] gathers, [1] incompatible images, [2] missing representatives
+};
+HxArgs make_args(const ed_hamiltonian* h);
+// One batched H.x launch (all sectors of a batch).
+struct BatchLaunch {
+    const HxArgs* desc;        // device [n_sec]
+    const int64_t* row_off;    // device [n_sec+1]
+    int n_sec;
+    int64_t total_rows;
+    size_t smem;
+    bool w8, chunked, ns_ok;
+    int n_sub;
+    ed_dtype dtype;
+    int nvec;
+    const void* x;
+    void* y;
+    const int* x_step;         // device step index or null
+    int64_t x_step_elems;
+    unsigned long long* counters;
+    int waves;                 // grid = SMs x resident blocks x waves
+};
+ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s);
+size_t hx_smem_bytes(const ed_hamiltonian* h);
 // implemented in ed_basis.cu
 ed_status basis_build_device(ed_basis* b, cudaStream_t s);
 ed_status upload_tables(ed_basis* b, cudaStream_t s);

@@ -56,6 +56,16 @@ class ed_lanczos_opts(ctypes.Structure):
                 ("seed", c_u64), ("refine", c_i32), ("check_every", c_i32)]
 
 
+class ed_block_lanczos_opts(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int), ("block", c_i32), ("n_eig", c_i32), ("tol", c_dbl), ("max_iter", c_i32),
+                ("seed", c_u64), ("use_graph", c_i32), ("check_every", c_i32)]
+
+
+class ed_block_lanczos_report(ctypes.Structure):
+    _fields_ = [("iters", c_i32), ("converged_sectors", c_i32), ("krylov_dim", c_i32), ("used_graph", c_i32),
+                ("seconds", c_dbl), ("step_seconds", c_dbl)]
+
+
 class ed_lanczos_report(ctypes.Structure):
     _fields_ = [("iters", c_i32), ("converged", c_i32), ("n_apply", c_i32), ("ritz", c_dbl * 8),
                 ("resid_bound", c_dbl * 8), ("refined", c_dbl * 8), ("refined_resid", c_dbl * 8),
@@ -87,6 +97,15 @@ def lib():
         L.ed_apply.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
         L.ed_apply_counters.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
         L.ed_lanczos.argtypes = [c_vp, P(ed_lanczos_opts), P(c_dbl), c_vp, P(ed_lanczos_report), c_vp]
+        L.ed_batch_create.argtypes = [P(c_vp), c_i32, P(c_vp)]
+        L.ed_batch_rows.argtypes = [c_vp, P(c_i64)]
+        L.ed_apply_batch.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
+        L.ed_batch_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp, P(c_i32)]
+        L.ed_batch_free.argtypes = [c_vp]
+        L.ed_batch_free.restype = None
+        L.ed_lanczos_batch.argtypes = [c_vp, P(ed_block_lanczos_opts), P(c_dbl), P(ed_block_lanczos_report), c_vp]
+        for f in ("ed_batch_create", "ed_batch_rows", "ed_apply_batch", "ed_batch_autotune", "ed_lanczos_batch"):
+            getattr(L, f).restype = ctypes.c_int
         L.ed_last_error.restype = ctypes.c_char_p
         L.ed_version.restype = ctypes.c_char_p
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
@@ -258,3 +277,67 @@ def report_dict(rep: ed_lanczos_report, n: int) -> dict:
     return dict(iters=rep.iters, converged=bool(rep.converged), n_apply=rep.n_apply, ritz=list(rep.ritz[:n]),
                 resid_bound=list(rep.resid_bound[:n]), refined=list(rep.refined[:n]),
                 refined_resid=list(rep.refined_resid[:n]), seconds=rep.seconds)
+
+
+class Batch:
+    """ed_batch_create / ed_apply_batch / ed_batch_autotune / ed_lanczos_batch."""
+
+    def __init__(self, hamiltonians):
+        self.hs = list(hamiltonians)
+        arr = (c_vp * len(self.hs))(*[h.handle for h in self.hs])
+        self.handle = c_vp()
+        check(lib().ed_batch_create(arr, len(self.hs), ctypes.byref(self.handle)))
+        ro = np.zeros(len(self.hs) + 1, np.int64)
+        check(lib().ed_batch_rows(self.handle, _ptr(ro, c_i64)))
+        self.row_off = ro
+        self.n = len(self.hs)
+        self.total = int(ro[-1])
+        self.is_real = all(h.is_real for h in self.hs)
+
+    @staticmethod
+    def _dt(x):
+        import torch
+        return {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64,
+                torch.complex128: ED_C128}[x.dtype]
+
+    def apply(self, x, y, nvec=1, stream=None):
+        """y = H x for concatenated vectors (nvec per sector, column-major within a sector)."""
+        import torch
+        if x.numel() != nvec * self.total or y.numel() != x.numel() or x.dtype != y.dtype:
+            raise ValueError("x, y must hold nvec * total rows of one dtype")
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        check(lib().ed_apply_batch(self.handle, self._dt(x), x.data_ptr(), y.data_ptr(), nvec, _stream_handle(stream)))
+        return y
+
+    def autotune(self, x, y, nvec=1, stream=None):
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        w = c_i32()
+        check(lib().ed_batch_autotune(self.handle, self._dt(x), x.data_ptr(), y.data_ptr(), nvec,
+                                      _stream_handle(stream), ctypes.byref(w)))
+        return int(w.value)
+
+    def lanczos(self, block=8, n_eig=3, tol=1e-10, max_iter=60, seed=1, use_graph=True, check_every=1,
+                dtype=None, raise_on_nonconv=True):
+        if dtype is None:
+            dtype = ED_F64 if self.is_real else ED_C128
+        o = ed_block_lanczos_opts(dtype, block, n_eig, tol, max_iter, seed, int(use_graph), check_every)
+        ev = np.zeros(self.n * n_eig, np.float64)
+        rep = ed_block_lanczos_report()
+        st = lib().ed_lanczos_batch(self.handle, ctypes.byref(o), _ptr(ev, c_dbl), ctypes.byref(rep), None)
+        if st != 0 and not (st == 11 and not raise_on_nonconv):
+            check(st)
+        return ev.reshape(self.n, n_eig), rep
+
+    def close(self):
+        if self.handle:
+            lib().ed_batch_free(self.handle)
+            self.handle = c_vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

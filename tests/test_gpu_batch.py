@@ -1,0 +1,78 @@
+"""Batches of sectors: the batched H.x equals per-sector H.x, and block Lanczos
+on all sectors at once reproduces each sector's oracle spectrum (with
+multiplicities up to the block size)."""
+import numpy as np
+import pytest
+
+import oracle
+from edinputs import configs as C
+from edinputs.vectors import state_vector
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_03511_gb300 import build
+    build.build()
+    import paper_2210_03511_gb300 as pkg
+    return pkg
+
+
+@pytest.fixture(scope="module")
+def tri12():
+    """All (k, rho_k) sectors of the 4x4 square torus with the rotation group C4
+    (abelian little groups, so 1-D irreps cover the space), J1=1, J2=0.3, Sz=0."""
+    return C.all_sectors("square", [[4, 0], [0, 4]], 1.0, 0.3, n_sublat=2, point="rot")
+
+
+def _concat(P, probs, nvec, seed, cplx):
+    blocks = []
+    for p in probs:
+        reps, _ = oracle.basis(p.sector)
+        blocks.append(np.concatenate([state_vector(seed + v, reps, complex_=cplx) for v in range(nvec)]))
+    return np.concatenate(blocks)
+
+
+def test_sector_dimensions_partition(tri12):
+    assert sum(oracle.sector_dim_formula(p.sector) for p in tri12) == oracle.binom(16, 8)
+
+
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_batched_apply_equals_per_sector(P, tri12, nvec):
+    import torch
+    bases = [P.Basis(p.sector) for p in tri12]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12)]
+    batch = P.Batch(hs)
+    X = _concat(P, tri12, nvec, 3, True)
+    x = torch.tensor(X, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    batch.apply(x, y, nvec=nvec)
+    torch.cuda.synchronize()
+    Y = y.cpu().numpy()
+    off = batch.row_off
+    for s, h in enumerate(hs):
+        D = int(off[s + 1] - off[s])
+        xs = x[nvec * int(off[s]):nvec * int(off[s + 1])].reshape(nvec, D).contiguous()
+        ys = torch.empty_like(xs)
+        h.apply(xs, ys)
+        torch.cuda.synchronize()
+        assert np.array_equal(ys.cpu().numpy().ravel(), Y[nvec * int(off[s]):nvec * int(off[s + 1])])
+    w = batch.autotune(x, y, nvec=nvec)
+    assert w in (1, 2, 4, 8, 16)
+
+
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_block_lanczos_all_sectors(P, tri12, use_graph):
+    bases = [P.Basis(p.sector) for p in tri12]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12)]
+    batch = P.Batch(hs)
+    n_eig = 3
+    ev, rep = batch.lanczos(block=4, n_eig=n_eig, tol=1e-12, max_iter=40, seed=5, use_graph=use_graph)
+    assert rep.converged_sectors == len(tri12) and rep.used_graph == int(use_graph)
+    for s, p in enumerate(tri12):
+        ref = np.linalg.eigvalsh(oracle.csr(p).toarray())[:n_eig]
+        assert np.allclose(ev[s, :len(ref)], ref, rtol=0, atol=1e-10 * max(1.0, abs(ref[0]))), (s, ev[s], ref)
