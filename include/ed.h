@@ -72,7 +72,8 @@ typedef enum { ED_F64 = 0, ED_F32 = 1, ED_C64 = 2, ED_C128 = 3 } ed_dtype;
 typedef struct CUstream_st* ed_stream;
 
 /* Device-memory provider.  alloc returns device memory of at least `bytes`
- * bytes usable on `stream`, or NULL; free releases it.  When the allocator
+ * bytes, aligned to 256 bytes, usable on `stream`, or NULL; free releases it.
+ * (Kernels read the basis with 16- and 32-byte vector loads.)  When the allocator
  * pointer passed to a call is NULL the library uses cudaMalloc/cudaFree. */
 typedef struct {
     void* (*alloc)(size_t bytes, ed_stream stream, void* ctx);

@@ -29,12 +29,23 @@ extern template ed_status apply_batch_kind<1>(const BatchLaunch&, cudaStream_t);
 extern template ed_status apply_batch_kind<2>(const BatchLaunch&, cudaStream_t);
 extern template ed_status apply_batch_kind<3>(const BatchLaunch&, cudaStream_t);
 
-static SmemLayout layout_for(const ed_hamiltonian* h) {
-    const ed_basis* b = h->basis;
-    return smem_layout(b->dt.blob_bytes, h->n_flip, h->n_jc, b->dt.G, 1 << b->ht.m);
+// Must agree with the kernel's template choice (launch_ns / batch_nv): the
+// block-count-specialised search runs for 2..4 blocks with packed entries.
+static bool generic_search(const ed_basis* b, bool ns_ok) {
+    return !(ns_ok && b->ht.n_sub >= 2 && b->ht.n_sub <= 4);
 }
 
-size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype) { return layout_for(h).total; }
+static int kind_of(ed_dtype dt) { return dt == ED_F64 ? 0 : dt == ED_F32 ? 1 : dt == ED_C128 ? 2 : 3; }
+
+static SmemLayout layout_for(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok) {
+    const ed_basis* b = h->basis;
+    return smem_layout(hot_bytes(b->dt, kind_of(dt), generic_search(b, ns_ok)), h->n_flip, h->n_jc, b->dt.G,
+                       1 << b->ht.m);
+}
+
+size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype dt) {
+    return layout_for(h, dt, h->basis->dt.dl_stride == 4).total;
+}
 
 HxArgs make_args(const ed_hamiltonian* h) {
     const ed_basis* b = h->basis;
@@ -46,6 +57,7 @@ HxArgs make_args(const ed_hamiltonian* h) {
     a.dir_base = (const uint32_t*)dir;
     a.dir_q = dir + b->dir_q_off();
     a.limits = (const uint32_t*)(dir + b->dir_lim_off());
+    a.bkt = b->bkt.p;
     a.L = b->prefix_bits;
     a.S = 1 << b->ht.m;
     a.flips = (const FlipTerm*)h->d_flips.p;
@@ -62,7 +74,7 @@ HxArgs make_args(const ed_hamiltonian* h) {
     return a;
 }
 
-size_t hx_smem_bytes(const ed_hamiltonian* h) { return layout_for(h).total; }
+size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok) { return layout_for(h, dt, ns_ok).total; }
 
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s) {
     switch (L.dtype) {
@@ -85,6 +97,7 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
     a.dir_base = (const uint32_t*)dir;
     a.dir_q = dir + b->dir_q_off();
     a.limits = (const uint32_t*)(dir + b->dir_lim_off());
+    a.bkt = b->bkt.p;
     a.L = b->prefix_bits;
     a.S = 1 << b->ht.m;
     a.flips = (const FlipTerm*)h->d_flips.p;
@@ -102,9 +115,9 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
     a.D = b->dim;
     a.counters = (unsigned long long*)h->d_counters.p;
     ED_CUDA(cudaMemsetAsync(h->d_counters.p, 0, 24, s));
-    const size_t smem = layout_for(h).total;
     const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
     const bool ns_ok = b->dt.dl_stride == 4;
+    const size_t smem = layout_for(h, dt, ns_ok).total;
     const int n_sub = b->ht.n_sub;
     switch (dt) {
         case ED_F64: return apply_launch_kind<0>(a, smem, n_sub, ns_ok, w8, ch, s);

@@ -75,8 +75,9 @@ __device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t 
     using V = Val<K>;
     using T = typename V::T;
     using R = typename V::R;
-    const SmemLayout lay = smem_layout(a.dt.blob_bytes, a.n_flip, a.n_jc, a.dt.G, a.S);
-    stage_blob(smem, a.dt.blob, a.dt.blob_bytes);
+    constexpr bool generic = !(NS >= 2 && NS <= 4);
+    const SmemLayout lay = smem_layout(hot_bytes(a.dt, K, generic), a.n_flip, a.n_jc, a.dt.G, a.S);
+    const TabView<CH> t = stage_hot<CH>(a.dt, smem, K, generic);
     stage_blob(smem + lay.flip, (const uint8_t*)a.flips, (size_t)a.n_flip * sizeof(FlipTerm));
     stage_blob(smem + lay.jhs, (const uint8_t*)a.jhs, (size_t)a.n_jc * (a.dt.G + 1) * 8);
     uint16_t* pab = (uint16_t*)(smem + lay.pab);
@@ -95,7 +96,6 @@ __device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t 
     for (int i = threadIdx.x; i <= a.S; i += blockDim.x) dir_base[i] = a.dir_base[i];
     for (int i = threadIdx.x; i < a.S; i += blockDim.x) dir_q[i] = a.dir_q[i];
     __syncthreads();
-    const TabView<CH> t = tab_view<CH>(smem, a.dt);
     const FlipTerm* flips = (const FlipTerm*)(smem + lay.flip);
     const double* jhs = (const double*)(smem + lay.jhs);
     const W* __restrict__ reps = (const W*)a.reps;
@@ -159,7 +159,7 @@ __device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t 
                     ++n_skip;
                     continue;
                 }
-                const int64_t jx = find_index<W>(rp, reps, dir_base, dir_q, a.limits, a.L);
+                const int64_t jx = find_index_b<W>(rp, reps, dir_base, dir_q, a.limits, (const W*)a.bkt, a.L);
                 if (jx < 0) {
                     ++n_miss;
                     continue;

@@ -220,6 +220,19 @@ __global__ void limits_kernel(const W* reps, uint64_t D, const uint32_t* seg_bas
     if (blockIdx.x == 0 && threadIdx.x == 0) limits[n_keys] = (uint32_t)D;
 }
 
+// First four states of every Limits bucket (all-ones where the bucket is
+// shorter): the index lookup compares a bucket of at most four states
+// without touching the basis array.
+template <typename W>
+__global__ void bucket_kernel(const W* reps, const uint32_t* limits, uint64_t n_keys, W* bkt) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t key = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; key < n_keys; key += stride) {
+        const uint32_t lo = limits[key], hi = limits[key + 1];
+#pragma unroll
+        for (uint32_t p = 0; p < 4; ++p) bkt[4 * key + p] = lo + p < hi ? reps[lo + p] : ~(W)0;
+    }
+}
+
 // ---------------------------------------------------------------- representatives of given states
 template <typename W, bool CH>
 __global__ void __launch_bounds__(256) rep_kernel(DevTables dt, const uint64_t* states, int64_t n, uint64_t* rep,
@@ -548,6 +561,14 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
     else
         limits_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, D, (const uint32_t*)base,
                                                   base + (S + 1) * 4, d_vlo, S, L, d_lim, keys);
+    ED_CUDA(cudaGetLastError());
+    b->bkt.bytes = 4 * keys * b->word;
+    b->bkt.p = b->alloc.get(b->bkt.bytes, s);
+    if (!b->bkt.p) return fail(ED_ERR_NOMEM, "bucket allocation");
+    if (b->word == 8)
+        bucket_kernel<uint64_t><<<g, 256, 0, s>>>((const uint64_t*)b->reps.p, d_lim, keys, (uint64_t*)b->bkt.p);
+    else
+        bucket_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, d_lim, keys, (uint32_t*)b->bkt.p);
     ED_CUDA(cudaGetLastError());
     ED_CUDA(cudaStreamSynchronize(s));
     b->n_keys = keys;

@@ -30,7 +30,7 @@ struct ed_batch {
     ed::DevBuf d_desc, d_row_off, d_counters, d_tiles;
     int n = 0;
     int64_t total = 0;
-    size_t smem = 0;
+    size_t smem[4] = {0, 0, 0, 0};   // per dtype
     bool w8 = false, chunked = false, ns_ok = false, all_real = true;
     int n_sub = 0;
     int waves[4][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}};  // [dtype][nvec>1]: tuned grid waves
@@ -374,8 +374,9 @@ static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n)
         B->all_real = B->all_real && h->is_real;
         desc[s] = make_args(h);
         B->row_off[s + 1] = B->row_off[s] + b->dim;
-        B->smem = std::max(B->smem, hx_smem_bytes(h));
     }
+    for (int s = 0; s < n; ++s)
+        for (int k = 0; k < 4; ++k) B->smem[k] = std::max(B->smem[k], hx_smem_bytes(hs[s], (ed_dtype)k, B->ns_ok));
     B->total = B->row_off[n];
     // reduction tiles: (sector, begin, end), TILE rows, never crossing sectors
     B->tiles.clear();
@@ -409,7 +410,7 @@ static BatchLaunch make_launch(const ed_batch* B, ed_dtype dt, const void* x, vo
     L.row_off = (const int64_t*)B->d_row_off.p;
     L.n_sec = B->n;
     L.total_rows = B->total;
-    L.smem = B->smem;
+    L.smem = B->smem[(int)dt];
     L.w8 = B->w8;
     L.chunked = B->chunked;
     L.ns_ok = B->ns_ok;

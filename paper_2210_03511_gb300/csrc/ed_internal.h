@@ -126,6 +126,7 @@ struct ed_basis {
     //   limits[n_keys+1] (uint32): first basis index of each bucket
     ed::DevBuf limits;
     uint64_t n_keys = 0;
+    ed::DevBuf bkt;             // [n_keys][4] states (word size), first states of each bucket
     int device = 0;
     size_t dir_q_off() const { return (size_t)((1 << ht.m) + 1) * 4; }
     size_t dir_lim_off() const { return dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15); }
@@ -157,6 +158,7 @@ struct HxArgs {
     const uint32_t* dir_base;
     const uint8_t* dir_q;
     const uint32_t* limits;
+    const void* bkt;              // [n_keys][4] first states of each Limits bucket
     int L, S;
     const FlipTerm* flips;
     int n_flip;
@@ -192,7 +194,7 @@ struct BatchLaunch {
     int waves;                 // grid = SMs x resident blocks x waves
 };
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s);
-size_t hx_smem_bytes(const ed_hamiltonian* h);
+size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok);
 // implemented in ed_basis.cu
 ed_status basis_build_device(ed_basis* b, cudaStream_t s);
 ed_status upload_tables(ed_basis* b, cudaStream_t s);
