@@ -73,10 +73,13 @@ def chain16():
     return chain(16, 1.0)
 
 
-def square32(irrep="A1", momentum="Gamma"):
-    """32-site tilted square cluster a1=(4,4), a2=(4,-4); J1=1, J2=0.5; T32 x C4v, Sz=0."""
+def square32(irrep="A1", momentum="Gamma", n_sublat=2):
+    """32-site tilted square cluster a1=(4,4), a2=(4,-4); J1=1, J2=0.5; T32 x C4v, Sz=0.
+    Two sublattice blocks of 16 sites (the checkerboard) by default: 8-site
+    blocks have a 64-element block group acting on 256 substates, so images
+    typically have 4-16 representative candidates; 16-site blocks have 1-2."""
     k = (0.0, 0.0) if momentum == "Gamma" else (PI, PI)
-    return square([[4, 4], [4, -4]], 1.0, 0.5, k=k, irrep=irrep)
+    return square([[4, 4], [4, -4]], 1.0, 0.5, k=k, irrep=irrep, n_sublat=n_sublat, max_table_bytes=4 << 20)
 
 
 def kagome36(spinflip=1, irrep="A"):

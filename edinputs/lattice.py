@@ -570,6 +570,19 @@ def choose_partition(cands, perm, flip, max_table_bytes: int, max_block: int = 1
 # --------------------------------------------------------------------------
 # problem assembly
 # --------------------------------------------------------------------------
+def _snap_roots(chi: np.ndarray) -> np.ndarray:
+    """Characters of 1-D irreps are roots of unity; exp(i k.t) evaluated in
+    floating point carries errors of ~1e-14 (|k.t| up to tens of radians).
+    Components within 1e-12 of 0, +-1/2 or +-1 are set to those values, so
+    real characters are exactly +-1 and e.g. exp(2 pi i/3) = -1/2 + i sqrt(3)/2."""
+    def snap(v):
+        for c in (0.0, 0.5, -0.5, 1.0, -1.0):
+            if abs(v - c) < 1e-12:
+                return c
+        return v
+    return np.array([complex(snap(z.real), snap(z.imag)) for z in np.asarray(chi, dtype=complex)])
+
+
 def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: int | None = None,
                   point: str = "full", translations: bool = True, k=(0.0, 0.0), irrep: str = "A1",
                   spinflip: int | None = None, max_table_bytes: int = 96 * 1024,
@@ -607,7 +620,7 @@ def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: i
     if irrep not in names:
         raise ValueError(f"irrep {irrep} not among 1-D irreps {names} of the little group")
     chi_p = dict(zip(little, dict(irr)[irrep]))
-    chi = np.array([np.exp(1j * (k @ t)) * chi_p[int(pi)] for t, pi in zip(trans, pidx)])
+    chi = _snap_roots(np.array([np.exp(1j * (k @ t)) * chi_p[int(pi)] for t, pi in zip(trans, pidx)]))
     flip = np.zeros(len(perm), dtype=np.uint8)
     if spinflip is not None:
         if 2 * n_up != N:
@@ -636,7 +649,9 @@ def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: i
     cands = sublattice_partitions(cl, sgk)
     if n_sublat is not None:
         cands = [c for c in cands if len(c) == n_sublat]
-    blocks = choose_partition(cands, perm, flip, max_table_bytes)
+    # blocks of up to 12 sites by default; an explicit block count may use up
+    # to 16 (the library's limit; such tables are read from global memory)
+    blocks = choose_partition(cands, perm, flip, max_table_bytes, max_block=16 if n_sublat is not None else 12)
     order = [i for b in blocks for i in b]         # new site -> old site
     new_of_old = np.empty(N, dtype=np.int64)
     new_of_old[order] = np.arange(N)

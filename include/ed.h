@@ -73,7 +73,7 @@ typedef struct CUstream_st* ed_stream;
 
 /* Device-memory provider.  alloc returns device memory of at least `bytes`
  * bytes, aligned to 256 bytes, usable on `stream`, or NULL; free releases it.
- * (Kernels read the basis with 16- and 32-byte vector loads.)  When the allocator
+ * (Kernels read tables and vectors with 16-byte vector loads.)  When the allocator
  * pointer passed to a call is NULL the library uses cudaMalloc/cudaFree. */
 typedef struct {
     void* (*alloc)(size_t bytes, ed_stream stream, void* ctx);
@@ -215,13 +215,34 @@ ed_status ed_apply(const ed_hamiltonian* h, ed_dtype dtype, const void* x, void*
  * vector) and number of images skipped as incompatible. */
 ed_status ed_apply_counters(const ed_hamiltonian* h, ed_stream stream, int64_t* gathers, int64_t* skipped);
 
+/* Time ed_apply on (x, y) with the launch sized for 1, 2, ... resident blocks
+ * per SM, up to the most the kernel's registers allow (one vector: 6 for real
+ * vectors and N <= 32, 4 for real vectors and N > 32 or complex FP32, 2 for
+ * complex FP64; several vectors: 2), and keep the fastest for this
+ * dtype and nvec class (nvec == 1 or > 1) in `h`.  Fewer resident blocks let
+ * each block keep more of the sublattice tables in shared memory; more
+ * blocks hide more memory latency.  Results of ed_apply do not depend on the
+ * choice (every row is computed by one thread in a fixed order).  Overwrites
+ * y; synchronous.  Writes the chosen count to *blocks_per_sm if non-NULL.
+ * Without a call, ed_apply uses the most blocks the registers allow. */
+ed_status ed_apply_autotune(ed_hamiltonian* h, ed_dtype dtype, const void* x, void* y, int32_t nvec,
+                            ed_stream stream, int32_t* blocks_per_sm);
+
+/* Set the resident blocks per SM that ed_apply sizes its launch for (for this
+ * dtype and nvec class); 0 restores the default.  ED_ERR_ARG unless
+ * 0 <= blocks_per_sm <= the limit listed at ed_apply_autotune. */
+ed_status ed_apply_set_blocks(ed_hamiltonian* h, ed_dtype dtype, int32_t nvec, int32_t blocks_per_sm);
+
 typedef struct {
     ed_dtype dtype;        /* vector type: F64/C128 plain, F32/C64 mixed (FP64 reductions) */
     int32_t n_eig;         /* lowest eigenvalues wanted, 1..8 */
     double tol;            /* convergence tolerance on eigenvalues (relative, e.g. 1e-10); with F32/C64
                               vectors the FP32 phase stops at max(tol, 1e-6) and tol applies to the refinement */
     int32_t max_iter;      /* Lanczos steps at most (<= 2000) */
-    int32_t reorth;        /* 1 = full reorthogonalisation (classical Gram-Schmidt twice) against stored vectors */
+    int32_t reorth;        /* 1 = full reorthogonalisation (classical Gram-Schmidt twice) against stored
+                              vectors; 0 = the plain three-term recursion (three vectors in memory): spurious
+                              copies of converged eigenvalues are removed from the Ritz values (Cullum-Willoughby
+                              test) and Ritz vectors come from a second pass of the recursion */
     uint64_t seed;         /* start vector v1(state) = keyed SplitMix64 uniform in [-1,1), normalised */
     int32_t refine;        /* mixed precision (F32/C64): at most this many FP64 Lanczos steps, started from the
                               FP32 Ritz vectors, refine the eigenvalues (0 = no refinement) */
@@ -247,12 +268,26 @@ typedef struct {
  * opts.refine and the vectors are FP32, else Ritz values).  Converged means,
  * for each wanted Ritz value theta, |theta_n - theta_{n-c}| <= tol max(1,|theta|)
  * between checks and a Lanczos residual bound r = beta |s_last| with
- * min(r, r^2/gap) <= tol max(1,|theta|).  evecs: DEVICE [n_eig][D] of the vector dtype,
- * or NULL (needs reorth = 1 to be filled).  Workspace comes from cudaMalloc
+ * min(r, r^2/gap) <= tol max(1,|theta|).  evecs: DEVICE [n_eig][D] of the vector dtype
+ * (normalised Ritz vectors), or NULL.  Without reorthogonalisation the Ritz
+ * vectors and the refinement's start vector cost a second pass of `iters`
+ * H.x applications.  Workspace comes from the basis's allocator
  * and is released before return.  Synchronous.  Returns
  * ED_ERR_NOT_CONVERGED if max_iter is reached first (results still written). */
 ed_status ed_lanczos(const ed_hamiltonian* h, const ed_lanczos_opts* opts, double* evals, void* evecs,
                      ed_lanczos_report* report, ed_stream stream);
+
+/* Lowest k eigenvalues of a Lanczos T-matrix (Eq. tmatrix: diagonal alpha[n],
+ * off-diagonal beta[n-1], HOST arrays) by Sturm bisection in FP64, the solver
+ * ed_lanczos uses.  filter = 1 applies its treatment of the plain recursion:
+ * Ritz values within 100 eps_vectors |T| of each other count once, and a
+ * value without such copies that is also an eigenvalue of T without its first
+ * row and column (within 1e3 eps_64 |T|) is dropped as spurious; eps_vectors
+ * is the unit roundoff of the Lanczos vectors (2^-53 for FP64, 2^-24 for FP32,
+ * or their epsilon).  Writes at most k values, ascending, to evals (HOST) and
+ * their number to *n_found.  Host only; no device is touched. */
+ed_status ed_tridiag_eigs(const double* alpha, const double* beta, int32_t n, int32_t k, double eps_vectors,
+                          int32_t filter, double* evals, int32_t* n_found);
 
 /* ---------------------------------------------------------------- batches of sectors
  * A batch groups Hamiltonians of several sectors of one cluster (same number

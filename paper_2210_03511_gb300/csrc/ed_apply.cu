@@ -37,14 +37,28 @@ static bool generic_search(const ed_basis* b, bool ns_ok) {
 
 static int kind_of(ed_dtype dt) { return dt == ED_F64 ? 0 : dt == ED_F32 ? 1 : dt == ED_C128 ? 2 : 3; }
 
-static SmemLayout layout_for(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok) {
+static HxPlan plan_for(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int blocks) {
     const ed_basis* b = h->basis;
-    return smem_layout(hot_bytes(b->dt, kind_of(dt), generic_search(b, ns_ok)), h->n_flip, h->n_jc, b->dt.G,
-                       1 << b->ht.m);
+    return hx_plan(b->dt, kind_of(dt), generic_search(b, ns_ok), blocks, h->n_flip, h->n_jc, 1 << b->ht.m);
 }
 
-size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype dt) {
-    return layout_for(h, dt, h->basis->dt.dl_stride == 4).total;
+size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec, int blocks) {
+    (void)nvec;
+    return plan_for(h, dt, ns_ok, blocks).lay.total;
+}
+
+// Default resident blocks per SM: the most the registers allow (see
+// hx_min_blocks); the staging plan keeps in shared memory what fits
+// beside them and reads the rest through L1/L2.  (Measured on the
+// workloads: occupancy pays more than staging the Rep/Sym tables.)
+int hx_default_blocks(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec) {
+    (void)ns_ok;
+    return hx_min_blocks(h->basis->word, nvec == 1 ? 1 : MAXV, kind_of(dt));
+}
+
+static int blocks_for(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec) {
+    const int t = h->tuned_blocks[kind_of(dt)][nvec > 1 ? 1 : 0];
+    return t > 0 ? t : hx_default_blocks(h, dt, ns_ok, nvec);
 }
 
 HxArgs make_args(const ed_hamiltonian* h) {
@@ -57,7 +71,6 @@ HxArgs make_args(const ed_hamiltonian* h) {
     a.dir_base = (const uint32_t*)dir;
     a.dir_q = dir + b->dir_q_off();
     a.limits = (const uint32_t*)(dir + b->dir_lim_off());
-    a.bkt = b->bkt.p;
     a.L = b->prefix_bits;
     a.S = 1 << b->ht.m;
     a.flips = (const FlipTerm*)h->d_flips.p;
@@ -71,10 +84,10 @@ HxArgs make_args(const ed_hamiltonian* h) {
     a.n_jc = h->n_jc;
     a.D = b->dim;
     a.nvec = 1;
+    a.blocks = 1;  // set per launch
     return a;
 }
 
-size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok) { return layout_for(h, dt, ns_ok).total; }
 
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s) {
     switch (L.dtype) {
@@ -97,7 +110,6 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
     a.dir_base = (const uint32_t*)dir;
     a.dir_q = dir + b->dir_q_off();
     a.limits = (const uint32_t*)(dir + b->dir_lim_off());
-    a.bkt = b->bkt.p;
     a.L = b->prefix_bits;
     a.S = 1 << b->ht.m;
     a.flips = (const FlipTerm*)h->d_flips.p;
@@ -117,7 +129,8 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
     ED_CUDA(cudaMemsetAsync(h->d_counters.p, 0, 24, s));
     const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
     const bool ns_ok = b->dt.dl_stride == 4;
-    const size_t smem = layout_for(h, dt, ns_ok).total;
+    a.blocks = blocks_for(h, dt, ns_ok, nvec);
+    const size_t smem = plan_for(h, dt, ns_ok, a.blocks).lay.total;
     const int n_sub = b->ht.n_sub;
     switch (dt) {
         case ED_F64: return apply_launch_kind<0>(a, smem, n_sub, ns_ok, w8, ch, s);
@@ -129,3 +142,50 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
 }
 
 }  // namespace ed
+
+extern "C" ed_status ed_apply_autotune(ed_hamiltonian* h, ed_dtype dtype, const void* x, void* y, int32_t nvec,
+                                       ed_stream stream, int32_t* blocks_out) {
+    using namespace ed;
+    if (!h || !x || !y) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > MAXV) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    cudaStream_t s = (cudaStream_t)stream;
+    int& slot = h->tuned_blocks[kind_of(dtype)][nvec > 1 ? 1 : 0];
+    const int top = hx_min_blocks(h->basis->word, nvec == 1 ? 1 : MAXV, kind_of(dtype));
+    cudaEvent_t e0, e1;
+    ED_CUDA(cudaEventCreate(&e0));
+    ED_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_b = 0;
+    ed_status st = ED_OK;
+    for (int b = 1; b <= top && st == ED_OK; ++b) {
+        slot = b;
+        st = apply_launch(h, dtype, x, y, nvec, s);  // warm-up (configures the instantiation)
+        if (st != ED_OK) break;
+        if (cudaEventRecord(e0, s) != cudaSuccess) { st = fail(ED_ERR_CUDA, "event record"); break; }
+        st = apply_launch(h, dtype, x, y, nvec, s);
+        if (st != ED_OK) break;
+        if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            st = fail(ED_ERR_CUDA, "event wait");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; best_b = b; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    slot = st == ED_OK ? best_b : 0;
+    if (blocks_out) *blocks_out = slot;
+    return st;
+}
+
+extern "C" ed_status ed_apply_set_blocks(ed_hamiltonian* h, ed_dtype dtype, int32_t nvec, int32_t blocks) {
+    using namespace ed;
+    if (!h) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > MAXV) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    if ((int)dtype < 0 || (int)dtype > 3) return fail(ED_ERR_ARG, "bad dtype");
+    const int top = hx_min_blocks(h->basis->word, nvec == 1 ? 1 : MAXV, kind_of(dtype));
+    if (blocks < 0 || blocks > top) return fail(ED_ERR_ARG, "blocks per SM out of range [0,%d]", top);
+    h->tuned_blocks[kind_of(dtype)][nvec > 1 ? 1 : 0] = blocks;
+    return ED_OK;
+}

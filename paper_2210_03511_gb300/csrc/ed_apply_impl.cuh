@@ -43,23 +43,81 @@ __device__ __forceinline__ void rep_of(W tau, const TabView<CH>& t, W& r, int& g
     else find_rep<W, CH>(tau, t, r, g, nst, cp);
 }
 
-// Shared layout: [table blob][flip terms][packed (pa,pb)][jhs table][jcls]
-// [class masks][Limits directory].
+// Resident blocks per SM an H.x instantiation is built for (its register
+// budget: 65536 / (256 x blocks) registers a thread).  Measured on the
+// workloads: one real vector with 32-bit states runs fastest at 6 (40
+// registers, a few spills: square32 3.8 -> 3.4 ms), with 64-bit states at 4
+// (fewer registers spill the 64-bit search state: square40 1.77 -> 2.7 s);
+// one complex-FP32 vector at 4 (kagome36 294 -> 186 ms); complex FP64 and
+// several vectors at 2.
+__host__ __device__ constexpr int hx_min_blocks(int wbytes, int nv, int k) {
+    return nv != 1 ? 2 : (k < 2 ? (wbytes == 4 ? 6 : 4) : (k == 3 ? 4 : 2));
+}
+
+// Shared layout: [staged table sections][flip terms][packed (pa,pb)][jhs
+// table][jcls][class masks][Limits directory, when staged].
 struct SmemLayout {
     size_t flip, pab, jhs, jcls, cmask, dir, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(size_t blob, int n_flip, int n_jc, int G, int S) {
+__host__ __device__ inline SmemLayout smem_layout(size_t tables, int n_flip, int n_jc, int G, int S, bool dir) {
     SmemLayout l;
     auto up16 = [](size_t v) { return (v + 15) & ~(size_t)15; };
-    l.flip = up16(blob);
+    l.flip = up16(tables);
     l.pab = up16(l.flip + (size_t)n_flip * sizeof(FlipTerm));
     l.jhs = up16(l.pab + (size_t)n_flip * 2);
     l.jcls = up16(l.jhs + (size_t)n_jc * (G + 1) * 8);
     l.cmask = up16(l.jcls + (size_t)n_flip);
     l.dir = up16(l.cmask + (size_t)n_jc * MAXW * 4);
-    l.total = up16(l.dir + (size_t)(S + 1) * 4 + S);
+    l.total = dir ? up16(l.dir + (size_t)(S + 1) * 4 + S) : l.dir;
     return l;
+}
+
+// What one H.x block keeps in shared memory.  The per-row data (flip terms,
+// coefficient table, class masks) always; then, while they fit the share of
+// the SM that `blocks` resident blocks leave, in order of accesses per
+// flipped image: packed entries and chi signs (every candidate), character
+// tables (every gather), the (source, map) table (generic search), the local
+// block maps (every composed block), the Limits directory (every gather),
+// Rep (every block of every image), Sym offsets and lists.  Host and device
+// evaluate the same function, so launch size and kernel layout agree.
+struct HxPlan {
+    uint32_t mask;
+    uint32_t table_bytes;
+    bool dir;
+    SmemLayout lay;
+};
+
+__host__ __device__ inline HxPlan hx_plan(const DevTables& d, int K, bool generic, int blocks, int n_flip,
+                                          int n_jc, int S) {
+    const size_t per_sm = 228 * 1024, reserved = 1024, max_block = 227 * 1024;
+    size_t limit = per_sm / (size_t)(blocks < 1 ? 1 : blocks) - reserved;
+    if (limit > max_block) limit = max_block;
+    const SmemLayout base = smem_layout(0, n_flip, n_jc, d.G, S, false);
+    const size_t dir_bytes = (((size_t)(S + 1) * 4 + S) + 15) & ~(size_t)15;
+    size_t used = base.total;
+    HxPlan p{0u, 0u, false, base};
+    auto take = [&](uint32_t sec) {
+        if (sec == SEC_SRC && !generic) return;
+        const size_t n = sec_bytes(d, sec, K);
+        if (used + n <= limit) {
+            p.mask |= sec;
+            p.table_bytes += (uint32_t)n;
+            used += n;
+        }
+    };
+    take(SEC_DL);
+    take(SEC_CHI);
+    take(SEC_SRC);
+    take(SEC_MAPS);
+    if (used + dir_bytes <= limit) {
+        p.dir = true;
+        used += dir_bytes;
+    }
+    take(SEC_REP);
+    take(SEC_SYM);
+    p.lay = smem_layout(p.table_bytes, n_flip, n_jc, d.G, S, p.dir);
+    return p;
 }
 
 struct Counts {
@@ -76,8 +134,9 @@ __device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t 
     using T = typename V::T;
     using R = typename V::R;
     constexpr bool generic = !(NS >= 2 && NS <= 4);
-    const SmemLayout lay = smem_layout(hot_bytes(a.dt, K, generic), a.n_flip, a.n_jc, a.dt.G, a.S);
-    const TabView<CH> t = stage_hot<CH>(a.dt, smem, K, generic);
+    const HxPlan plan = hx_plan(a.dt, K, generic, a.blocks, a.n_flip, a.n_jc, a.S);
+    const SmemLayout lay = plan.lay;
+    const TabView<CH> t = stage_sections<CH>(a.dt, smem, K, plan.mask);
     stage_blob(smem + lay.flip, (const uint8_t*)a.flips, (size_t)a.n_flip * sizeof(FlipTerm));
     stage_blob(smem + lay.jhs, (const uint8_t*)a.jhs, (size_t)a.n_jc * (a.dt.G + 1) * 8);
     uint16_t* pab = (uint16_t*)(smem + lay.pab);
@@ -91,10 +150,16 @@ __device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t 
         jcls[i] = a.jcls[i];
         atomicOr(&cmask[a.jcls[i] * MAXW + (i >> 5)], 1u << (i & 31));
     }
-    uint32_t* dir_base = (uint32_t*)(smem + lay.dir);
-    uint8_t* dir_q = (uint8_t*)(dir_base + a.S + 1);
-    for (int i = threadIdx.x; i <= a.S; i += blockDim.x) dir_base[i] = a.dir_base[i];
-    for (int i = threadIdx.x; i < a.S; i += blockDim.x) dir_q[i] = a.dir_q[i];
+    const uint32_t* dir_base = a.dir_base;
+    const uint8_t* dir_q = a.dir_q;
+    if (plan.dir) {
+        uint32_t* db = (uint32_t*)(smem + lay.dir);
+        uint8_t* dq = (uint8_t*)(db + a.S + 1);
+        for (int i = threadIdx.x; i <= a.S; i += blockDim.x) db[i] = a.dir_base[i];
+        for (int i = threadIdx.x; i < a.S; i += blockDim.x) dq[i] = a.dir_q[i];
+        dir_base = db;
+        dir_q = dq;
+    }
     __syncthreads();
     const FlipTerm* flips = (const FlipTerm*)(smem + lay.flip);
     const double* jhs = (const double*)(smem + lay.jhs);
@@ -159,7 +224,7 @@ __device__ __forceinline__ void hx_body(const HxArgs& a, uint8_t* smem, int64_t 
                     ++n_skip;
                     continue;
                 }
-                const int64_t jx = find_index_b<W>(rp, reps, dir_base, dir_q, a.limits, (const W*)a.bkt, a.L);
+                const int64_t jx = find_index<W>(rp, reps, dir_base, dir_q, a.limits, a.L);
                 if (jx < 0) {
                     ++n_miss;
                     continue;
@@ -248,7 +313,7 @@ __device__ __forceinline__ void flush_counts(Counts c, unsigned long long* count
 }
 
 template <typename W, bool CH, int K, int NV, int NS>
-__global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2) hx_kernel(HxArgs a) {
+__global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), NV, K)) hx_kernel(HxArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
     Counts c;
     hx_body<W, CH, K, NV, NS>(a, smem, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, a.D,
@@ -263,10 +328,10 @@ __global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2) hx_kernel(H
 // block-stride loop.  Vectors are concatenated: sector s's block of nvec
 // vectors starts at element nvec*row_off[s] of x and y.
 template <typename W, bool CH, int K, int NV, int NS>
-__global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2)
+__global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), NV, K))
     hx_batch_kernel(const HxArgs* __restrict__ desc, const int64_t* __restrict__ row_off, int n_sec, int64_t chunk,
                     const void* x, void* y, int nvec, const int* __restrict__ x_step, int64_t x_step_elems,
-                    unsigned long long* counters) {
+                    unsigned long long* counters, int blocks) {
     using T = typename Val<K>::T;
     // optional device-side block index: x advances by x_step_elems per step
     // (lets one captured launch serve every step of a block Lanczos run)
@@ -287,6 +352,7 @@ __global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2)
         for (int sct = lo; sct < n_sec && row_off[sct] < g1; ++sct) {
             HxArgs a = desc[sct];
             a.nvec = nvec;
+            a.blocks = blocks;
             const int64_t off = row_off[sct];
             a.x = (const T*)x + (int64_t)a.nvec * off;
             a.y = (T*)y + (int64_t)a.nvec * off;
@@ -298,10 +364,10 @@ __global__ void __launch_bounds__(BLOCK, (NV == 1 && K < 2) ? 4 : 2)
 }
 
 
-template <typename W, bool CH, int K, int NV, int NS>
-static ed_status launch(const HxArgs& a, size_t smem, cudaStream_t s) {
-    auto k = hx_kernel<W, CH, K, NV, NS>;
-    static int cfg_smem = -1, cfg_grid = 0;  // per instantiation
+// Resident blocks per SM of one instantiation at `smem` bytes (cached per
+// instantiation for the last size asked).
+template <typename KernelT>
+static ed_status occupancy(KernelT k, size_t smem, int& cfg_smem, int& cfg_per_sm, int& cfg_sms) {
     if ((int)smem != cfg_smem) {
         ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         int dev = 0, sms = 0, per_sm = 0;
@@ -310,9 +376,20 @@ static ed_status launch(const HxArgs& a, size_t smem, cudaStream_t s) {
         ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, smem));
         if (per_sm < 1) return fail(ED_ERR_TABLE_TOO_LARGE, "H.x shared memory (%zu bytes) exceeds the device limit", smem);
         cfg_smem = (int)smem;
-        cfg_grid = sms * per_sm;
+        cfg_per_sm = per_sm;
+        cfg_sms = sms;
     }
-    int64_t grid = std::min<int64_t>(cfg_grid, (a.D + BLOCK - 1) / BLOCK);
+    return ED_OK;
+}
+
+template <typename W, bool CH, int K, int NV, int NS>
+static ed_status launch(const HxArgs& a, size_t smem, cudaStream_t s) {
+    auto k = hx_kernel<W, CH, K, NV, NS>;
+    static int cfg_smem = -1, cfg_per_sm = 0, cfg_sms = 0;  // per instantiation
+    const ed_status st = occupancy(k, smem, cfg_smem, cfg_per_sm, cfg_sms);
+    if (st != ED_OK) return st;
+    const int per_sm = std::min(cfg_per_sm, std::max(1, a.blocks));
+    int64_t grid = std::min<int64_t>((int64_t)cfg_sms * per_sm, (a.D + BLOCK - 1) / BLOCK);
     if (grid < 1) grid = 1;
     k<<<(unsigned)grid, BLOCK, smem, s>>>(a);
     ED_CUDA(cudaGetLastError());
@@ -338,18 +415,15 @@ static ed_status launch_nv(const HxArgs& a, size_t smem, int n_sub, bool ns_ok, 
 template <typename W, bool CH, int K, int NV, int NS>
 static ed_status launch_batch(const BatchLaunch& L, cudaStream_t s) {
     auto k = hx_batch_kernel<W, CH, K, NV, NS>;
-    ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem));
-    int per_sm = 0;
-    ED_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, BLOCK, L.smem));
-    if (per_sm < 1) return fail(ED_ERR_TABLE_TOO_LARGE, "batched H.x shared memory (%zu bytes) exceeds the limit", L.smem);
-    int dev = 0, sms = 0;
-    ED_CUDA(cudaGetDevice(&dev));
-    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const int64_t grid = std::max<int64_t>(1, (int64_t)sms * per_sm * std::max(1, L.waves));
+    static int cfg_smem = -1, cfg_per_sm = 0, cfg_sms = 0;  // per instantiation
+    const ed_status st = occupancy(k, L.smem, cfg_smem, cfg_per_sm, cfg_sms);
+    if (st != ED_OK) return st;
+    const int per_sm = std::min(cfg_per_sm, std::max(1, L.blocks));
+    const int64_t grid = std::max<int64_t>(1, (int64_t)cfg_sms * per_sm * std::max(1, L.waves));
     const int64_t chunk = std::max<int64_t>(1, (L.total_rows + grid - 1) / grid);
     const int64_t nblk = (L.total_rows + chunk - 1) / chunk;
     k<<<(unsigned)nblk, BLOCK, L.smem, s>>>(L.desc, L.row_off, L.n_sec, chunk, L.x, L.y, L.nvec, L.x_step,
-                                               L.x_step_elems, L.counters);
+                                               L.x_step_elems, L.counters, L.blocks);
     ED_CUDA(cudaGetLastError());
     return ED_OK;
 }

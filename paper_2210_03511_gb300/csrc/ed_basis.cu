@@ -69,9 +69,7 @@ struct EnumArgs {
 template <typename W, bool CHK, int PASS>
 __global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
     extern __shared__ __align__(16) uint8_t smem[];
-    stage_blob(smem, a.dt.blob, a.dt.blob_bytes);
-    __syncthreads();
-    const TabView<CHK> t = tab_view<CHK>(smem, a.dt);
+    const TabView<CHK> t = stage_whole_or_global<CHK>(a.dt, smem);
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; c < a.n_chunks; c += stride) {
         // segment of chunk c
@@ -220,27 +218,12 @@ __global__ void limits_kernel(const W* reps, uint64_t D, const uint32_t* seg_bas
     if (blockIdx.x == 0 && threadIdx.x == 0) limits[n_keys] = (uint32_t)D;
 }
 
-// First four states of every Limits bucket (all-ones where the bucket is
-// shorter): the index lookup compares a bucket of at most four states
-// without touching the basis array.
-template <typename W>
-__global__ void bucket_kernel(const W* reps, const uint32_t* limits, uint64_t n_keys, W* bkt) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    for (uint64_t key = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; key < n_keys; key += stride) {
-        const uint32_t lo = limits[key], hi = limits[key + 1];
-#pragma unroll
-        for (uint32_t p = 0; p < 4; ++p) bkt[4 * key + p] = lo + p < hi ? reps[lo + p] : ~(W)0;
-    }
-}
-
 // ---------------------------------------------------------------- representatives of given states
 template <typename W, bool CH>
 __global__ void __launch_bounds__(256) rep_kernel(DevTables dt, const uint64_t* states, int64_t n, uint64_t* rep,
                                                   int32_t* gout, int32_t* nst, uint8_t* cmp) {
     extern __shared__ __align__(16) uint8_t smem[];
-    stage_blob(smem, dt.blob, dt.blob_bytes);
-    __syncthreads();
-    const TabView<CH> t = tab_view<CH>(smem, dt);
+    const TabView<CH> t = stage_whole_or_global<CH>(dt, smem);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         W r;
         int g, ns;
@@ -257,7 +240,7 @@ template <typename W, bool CH>
 static ed_status launch_rep(const ed_basis* b, const uint64_t* st, int64_t n, uint64_t* r, int32_t* g, int32_t* ns,
                             uint8_t* cp, cudaStream_t s) {
     auto k = rep_kernel<W, CH>;
-    const size_t smem = b->dt.blob_bytes;
+    const size_t smem = whole_stage_bytes(b->dt);
     ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const unsigned grid = (unsigned)std::min<int64_t>((n + 255) / 256, 1024);
     k<<<grid, 256, smem, s>>>(b->dt, st, n, r, g, ns, cp);
@@ -419,7 +402,7 @@ static ed_status enum_both(ed_basis* b, EnumArgs& a, size_t smem, int sms, cudaS
 }
 
 static ed_status run_enum(ed_basis* b, EnumArgs& a, int pass, int sms, cudaStream_t s) {
-    const size_t smem = b->dt.blob_bytes;
+    const size_t smem = whole_stage_bytes(b->dt);
     const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
     if (w8) return ch ? enum_both<uint64_t, true>(b, a, smem, sms, s, pass)
                       : enum_both<uint64_t, false>(b, a, smem, sms, s, pass);
@@ -561,14 +544,6 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
     else
         limits_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, D, (const uint32_t*)base,
                                                   base + (S + 1) * 4, d_vlo, S, L, d_lim, keys);
-    ED_CUDA(cudaGetLastError());
-    b->bkt.bytes = 4 * keys * b->word;
-    b->bkt.p = b->alloc.get(b->bkt.bytes, s);
-    if (!b->bkt.p) return fail(ED_ERR_NOMEM, "bucket allocation");
-    if (b->word == 8)
-        bucket_kernel<uint64_t><<<g, 256, 0, s>>>((const uint64_t*)b->reps.p, d_lim, keys, (uint64_t*)b->bkt.p);
-    else
-        bucket_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, d_lim, keys, (uint32_t*)b->bkt.p);
     ED_CUDA(cudaGetLastError());
     ED_CUDA(cudaStreamSynchronize(s));
     b->n_keys = keys;

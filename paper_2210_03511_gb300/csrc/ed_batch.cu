@@ -30,7 +30,8 @@ struct ed_batch {
     ed::DevBuf d_desc, d_row_off, d_counters, d_tiles;
     int n = 0;
     int64_t total = 0;
-    size_t smem[4] = {0, 0, 0, 0};   // per dtype
+    size_t smem[4][2] = {};   // per dtype, for one / several vectors
+    int blocks[4][2] = {};    // resident blocks per SM, same index
     bool w8 = false, chunked = false, ns_ok = false, all_real = true;
     int n_sub = 0;
     int waves[4][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}};  // [dtype][nvec>1]: tuned grid waves
@@ -375,8 +376,16 @@ static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n)
         desc[s] = make_args(h);
         B->row_off[s + 1] = B->row_off[s] + b->dim;
     }
-    for (int s = 0; s < n; ++s)
-        for (int k = 0; k < 4; ++k) B->smem[k] = std::max(B->smem[k], hx_smem_bytes(hs[s], (ed_dtype)k, B->ns_ok));
+    // every sector's tables must fit the batch's staging plan: the fewest
+    // resident blocks any sector needs
+    for (int k = 0; k < 4; ++k)
+        for (int v = 0; v < 2; ++v) {
+            int bl = 4;
+            for (int s = 0; s < n; ++s) bl = std::min(bl, hx_default_blocks(hs[s], (ed_dtype)k, B->ns_ok, v ? 8 : 1));
+            B->blocks[k][v] = bl;
+            for (int s = 0; s < n; ++s)
+                B->smem[k][v] = std::max(B->smem[k][v], hx_smem_bytes(hs[s], (ed_dtype)k, B->ns_ok, v ? 8 : 1, bl));
+        }
     B->total = B->row_off[n];
     // reduction tiles: (sector, begin, end), TILE rows, never crossing sectors
     B->tiles.clear();
@@ -410,7 +419,8 @@ static BatchLaunch make_launch(const ed_batch* B, ed_dtype dt, const void* x, vo
     L.row_off = (const int64_t*)B->d_row_off.p;
     L.n_sec = B->n;
     L.total_rows = B->total;
-    L.smem = B->smem[(int)dt];
+    L.smem = B->smem[(int)dt][nvec > 1 ? 1 : 0];
+    L.blocks = B->blocks[(int)dt][nvec > 1 ? 1 : 0];
     L.w8 = B->w8;
     L.chunked = B->chunked;
     L.ns_ok = B->ns_ok;

@@ -78,21 +78,33 @@ ED_HD TabView<CHUNKED> tab_view(const uint8_t* base, const DevTables& d) {
     return v;
 }
 
-// Bytes of the table sections an H.x kernel keeps in shared memory: the
-// representative search always needs Rep, Sym, the maps, the packed entries,
-// the character classes and signs; the generic search also the (source, map)
-// table; complex and FP32 kinds also their character / sqrt tables.  Other
-// sections are read from global memory.
-ED_HD size_t hot_bytes(const DevTables& d, int K, bool generic) {
-    size_t n = (size_t)(d.off_src - d.off_rep)          // rep, sym_off, sym_ids, maps
-               + (size_t)(d.off_sqrt - d.off_chicls)     // chi_cls
-               + (size_t)(d.blob_bytes - d.off_dl);      // dl, chi_neg
-    if (generic) n += (size_t)(d.off_chi - d.off_src);
-    if (K == 2) n += (size_t)(d.off_chicls - d.off_chi) + (size_t)(d.off_chif - d.off_sqrt);
-    if (K == 1 || K == 3) n += (size_t)(d.off_sqrtf - d.off_chif) + (size_t)(d.off_dl - d.off_sqrtf);
-    return n;
-}
+// Table images up to this size are staged whole into shared memory by the
+// basis and representative kernels; larger images (blocks of up to 16 sites)
+// are read from global memory, where they stay L2-resident.
+constexpr size_t kStageWholeLimit = 200 * 1024;
 
+// Table sections an H.x block may stage into shared memory (the others are
+// read from the global image): the packed entries and chi sign bits, the
+// character tables of the vector kind, the (source, map) table of the
+// generic search, the local block maps, Rep, Sym offsets and lists.
+enum : uint32_t { SEC_DL = 1u, SEC_CHI = 2u, SEC_SRC = 4u, SEC_MAPS = 8u, SEC_REP = 16u, SEC_SYM = 32u };
+
+ED_HD uint32_t sec_bytes(const DevTables& d, uint32_t sec, int K) {
+    switch (sec) {
+        case SEC_DL: return (uint32_t)d.blob_bytes - d.off_dl;  // dl, chi_neg
+        case SEC_CHI: {
+            uint32_t n = d.off_sqrt - d.off_chicls;  // chi_cls
+            if (K == 2) n += (d.off_chicls - d.off_chi) + (d.off_chif - d.off_sqrt);
+            if (K == 1 || K == 3) n += (d.off_sqrtf - d.off_chif) + (d.off_dl - d.off_sqrtf);
+            return n;
+        }
+        case SEC_SRC: return d.off_chi - d.off_src;
+        case SEC_MAPS: return d.off_src - d.off_sa;
+        case SEC_REP: return d.off_symoff - d.off_rep;
+        case SEC_SYM: return d.off_sa - d.off_symoff;  // sym_off, sym_ids
+    }
+    return 0;
+}
 
 // Cooperative copy of a table image into shared memory (16-byte chunks).
 __device__ __forceinline__ void stage_blob(uint8_t* dst, const uint8_t* src, size_t bytes) {
@@ -102,10 +114,11 @@ __device__ __forceinline__ void stage_blob(uint8_t* dst, const uint8_t* src, siz
     for (size_t i = threadIdx.x; i < n4; i += blockDim.x) d4[i] = s4[i];
 }
 
-// Stage the hot sections (see hot_bytes) into shared memory; the returned
-// view points there for them and into the global image for the rest.
+// Stage the sections of `mask` into shared memory; the returned view points
+// there for them and into the global image for the rest.  Every section
+// starts and ends on a 16-byte boundary of the image.
 template <bool CHUNKED>
-__device__ __forceinline__ TabView<CHUNKED> stage_hot(const DevTables& d, uint8_t* smem, int K, bool generic) {
+__device__ __forceinline__ TabView<CHUNKED> stage_sections(const DevTables& d, uint8_t* smem, int K, uint32_t mask) {
     TabView<CHUNKED> t = tab_view<CHUNKED>(d.blob, d);
     size_t pos = 0;
     auto put = [&](uint32_t off, uint32_t end) -> const uint8_t* {
@@ -114,27 +127,47 @@ __device__ __forceinline__ TabView<CHUNKED> stage_hot(const DevTables& d, uint8_
         pos += end - off;
         return p;
     };
-    const uint8_t* b = put(d.off_rep, d.off_src);
-    t.rep = (const uint16_t*)b;
-    t.sym_off = (const uint32_t*)(b + (d.off_symoff - d.off_rep));
-    t.sym_ids = (const uint16_t*)(b + (d.off_symids - d.off_rep));
-    t.lmap = (const void*)(b + (d.off_sa - d.off_rep));
-    t.chi_cls = (const uint16_t*)put(d.off_chicls, d.off_sqrt);
-    const uint8_t* e = put(d.off_dl, (uint32_t)d.blob_bytes);
-    t.dl = (const uint16_t*)e;
-    t.chi_neg = e + (d.off_chineg - d.off_dl);
-    if (generic) t.srclid = (const uint32_t*)put(d.off_src, d.off_chi);
-    if (K == 2) {
-        t.chi = (const double2*)put(d.off_chi, d.off_chicls);
-        t.sqrtn = (const double*)put(d.off_sqrt, d.off_chif);
-        t.isqrtn = t.sqrtn + (d.G + 1);
+    if (mask & SEC_DL) {
+        const uint8_t* e = put(d.off_dl, (uint32_t)d.blob_bytes);
+        t.dl = (const uint16_t*)e;
+        t.chi_neg = e + (d.off_chineg - d.off_dl);
     }
-    if (K == 1 || K == 3) {
-        t.chif = (const float2*)put(d.off_chif, d.off_sqrtf);
-        t.sqrtnf = (const float*)put(d.off_sqrtf, d.off_dl);
-        t.isqrtnf = t.sqrtnf + (d.G + 1);
+    if (mask & SEC_CHI) {
+        t.chi_cls = (const uint16_t*)put(d.off_chicls, d.off_sqrt);
+        if (K == 2) {
+            t.chi = (const double2*)put(d.off_chi, d.off_chicls);
+            t.sqrtn = (const double*)put(d.off_sqrt, d.off_chif);
+            t.isqrtn = t.sqrtn + (d.G + 1);
+        }
+        if (K == 1 || K == 3) {
+            t.chif = (const float2*)put(d.off_chif, d.off_sqrtf);
+            t.sqrtnf = (const float*)put(d.off_sqrtf, d.off_dl);
+            t.isqrtnf = t.sqrtnf + (d.G + 1);
+        }
+    }
+    if (mask & SEC_SRC) t.srclid = (const uint32_t*)put(d.off_src, d.off_chi);
+    if (mask & SEC_MAPS) t.lmap = (const void*)put(d.off_sa, d.off_src);
+    if (mask & SEC_REP) t.rep = (const uint16_t*)put(d.off_rep, d.off_symoff);
+    if (mask & SEC_SYM) {
+        const uint8_t* b = put(d.off_symoff, d.off_sa);
+        t.sym_off = (const uint32_t*)b;
+        t.sym_ids = (const uint16_t*)(b + (d.off_symids - d.off_symoff));
     }
     return t;
+}
+
+// Whole image in shared memory when it fits kStageWholeLimit, else the
+// global image.  All threads of the block must call it (it synchronises).
+template <bool CHUNKED>
+__device__ __forceinline__ TabView<CHUNKED> stage_whole_or_global(const DevTables& d, uint8_t* smem) {
+    const bool staged = d.blob_bytes <= kStageWholeLimit;
+    if (staged) stage_blob(smem, d.blob, d.blob_bytes);
+    __syncthreads();
+    return tab_view<CHUNKED>(staged ? smem : d.blob, d);
+}
+
+ED_HD size_t whole_stage_bytes(const DevTables& d) {
+    return d.blob_bytes <= kStageWholeLimit ? d.blob_bytes : 0;
 }
 
 template <typename W>
@@ -332,40 +365,6 @@ ED_HD bool is_rep(W s, const TabView<CHUNKED>& t, int& nstab, bool& compat) {
     nstab = ns;
     compat = cp;
     return true;
-}
-
-// Bucket-inline variant: bkt holds the first 4 states of every Limits bucket
-// (padded with all-ones), so the bucket bounds and its states are fetched
-// together and a bucket of at most 4 states needs no dependent search.
-template <typename W>
-ED_HD int64_t find_index_b(W r, const W* __restrict__ reps, const uint32_t* __restrict__ dir_base,
-                           const uint8_t* __restrict__ dir_q, const uint32_t* __restrict__ limits,
-                           const W* __restrict__ bkt, int L) {
-    const uint32_t top = (uint32_t)(r >> L);
-    const int q = dir_q[top];
-    const W low = L ? (r & (((W)1 << L) - 1)) : (W)0;
-    const uint32_t key = dir_base[top] + (q ? (uint32_t)(low >> (L - q)) : 0u);
-    uint32_t lo = ld_ro(limits + key), hi = ld_ro(limits + key + 1);
-    const W* bk = bkt + 4 * (size_t)key;
-    W b0, b1, b2, b3;
-    if constexpr (sizeof(W) == 4) {
-        const uint4 v = ld_ro((const uint4*)bk);
-        b0 = v.x; b1 = v.y; b2 = v.z; b3 = v.w;
-    } else {
-        const ulonglong2 u = ld_ro((const ulonglong2*)bk), w = ld_ro((const ulonglong2*)bk + 1);
-        b0 = u.x; b1 = u.y; b2 = w.x; b3 = w.y;
-    }
-    if (hi - lo <= 4u) {
-        const int p = (b0 == r) ? 0 : (b1 == r) ? 1 : (b2 == r) ? 2 : (b3 == r) ? 3 : -1;
-        return (p >= 0 && (uint32_t)p < hi - lo) ? (int64_t)(lo + p) : -1;
-    }
-    const uint32_t end = hi;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (ld_ro(reps + mid) < r) lo = mid + 1;
-        else hi = mid;
-    }
-    return (lo < end && ld_ro(reps + lo) == r) ? (int64_t)lo : -1;
 }
 
 // Index of representative r (section "Distributed and hybrid memory

@@ -504,7 +504,6 @@ void ed_basis_free(ed_basis* b) {
     b->alloc.put(b->reps.p, b->reps.bytes, 0);
     b->alloc.put(b->stab.p, b->stab.bytes, 0);
     b->alloc.put(b->limits.p, b->limits.bytes, 0);
-    b->alloc.put(b->bkt.p, b->bkt.bytes, 0);
     b->alloc.put(b->tables.p, b->tables.bytes, 0);
     delete b;
 }

@@ -126,7 +126,6 @@ struct ed_basis {
     //   limits[n_keys+1] (uint32): first basis index of each bucket
     ed::DevBuf limits;
     uint64_t n_keys = 0;
-    ed::DevBuf bkt;             // [n_keys][4] states (word size), first states of each bucket
     int device = 0;
     size_t dir_q_off() const { return (size_t)((1 << ht.m) + 1) * 4; }
     size_t dir_lim_off() const { return dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15); }
@@ -147,6 +146,7 @@ struct ed_hamiltonian {
     std::vector<double> jhs;
     std::vector<uint8_t> jcls;          // [n_flip]
     ed::DevBuf d_jhs, d_jcls;
+    int tuned_blocks[4][2] = {};        // resident H.x blocks per SM by dtype, nvec == 1 / > 1 (0: default)
 };
 
 namespace ed {
@@ -158,8 +158,8 @@ struct HxArgs {
     const uint32_t* dir_base;
     const uint8_t* dir_q;
     const uint32_t* limits;
-    const void* bkt;              // [n_keys][4] first states of each Limits bucket
     int L, S;
+    int blocks;                   // resident blocks per SM the launch is sized for (drives the staging plan)
     const FlipTerm* flips;
     int n_flip;
     const int8_t* diag_pos;       // [2*n_diag_bonds] bit positions, bonds sorted by class
@@ -192,9 +192,11 @@ struct BatchLaunch {
     int64_t x_step_elems;
     unsigned long long* counters;
     int waves;                 // grid = SMs x resident blocks x waves
+    int blocks;                // resident blocks per SM (staging plan of every sector)
 };
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s);
-size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok);
+size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec, int blocks);
+int hx_default_blocks(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec);
 // implemented in ed_basis.cu
 ed_status basis_build_device(ed_basis* b, cudaStream_t s);
 ed_status upload_tables(ed_basis* b, cudaStream_t s);
@@ -205,7 +207,6 @@ ed_status representatives_static(const ed_sector* sector, const uint64_t* states
                                  int32_t* nstab, uint8_t* compat, cudaStream_t s);
 // implemented in ed_apply.cu
 ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
-size_t apply_smem_bytes(const ed_hamiltonian* h, ed_dtype dt);
 // implemented in ed_lanczos.cu
 ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
                       ed_lanczos_report* rep, cudaStream_t s);

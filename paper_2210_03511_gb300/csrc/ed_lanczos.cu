@@ -155,6 +155,21 @@ __global__ void combine(O* out, const typename LV<K>::T* A, int64_t ld, int nk, 
     }
 }
 
+// out_k += c[k] v for k < nk (out_k = out + k*ldo): the second pass of the
+// plain recursion builds Ritz vectors one Lanczos vector at a time
+template <int K, typename O>
+__global__ void accumulate(O* out, int64_t ldo, int nk, const double* c, const typename LV<K>::T* v, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 a = ld2(v[i]);
+        for (int k = 0; k < nk; ++k) {
+            double2 x = ld2(out[(int64_t)k * ldo + i]);
+            x.x += c[k] * a.x;
+            x.y += c[k] * a.y;
+            st2(out[(int64_t)k * ldo + i], x);
+        }
+    }
+}
+
 // dst = src * (1/norm), norm = sqrt(Re nrm2->x) unless given as beta
 template <int K>
 __global__ void scale_by(typename LV<K>::T* dst, const typename LV<K>::T* src, int64_t n, const double* beta) {
@@ -282,6 +297,62 @@ static void tri_eig(const std::vector<double>& a, const std::vector<double>& b, 
     }
 }
 
+// Lowest k eigenpairs of T after removing the spurious copies that the plain
+// recursion (no reorthogonalisation) produces once Lanczos vectors lose
+// orthogonality (Cullum and Willoughby, "Lanczos Algorithms for Large
+// Symmetric Eigenvalue Computations", 1985).  Ritz values within `cluster` of
+// each other are copies of one eigenvalue and count once; a value without
+// copies that is also an eigenvalue of T^ (T without its first row and
+// column, within `cw`) is spurious and dropped.  Each kept value gets a
+// T-eigenvector by inverse iteration (for a multiple value: a vector of the
+// near-invariant subspace of its copies).
+static void tri_eig_filtered(const std::vector<double>& a, const std::vector<double>& b, int n, int k,
+                             double cluster, double cw, std::vector<double>& lam,
+                             std::vector<std::vector<double>>& vec) {
+    lam.clear();
+    std::vector<double> ah(a.begin() + 1, a.begin() + n), bh;
+    if (n > 2) bh.assign(b.begin() + 1, b.begin() + n - 1);
+    bh.resize(std::max(0, n - 1), 0.0);
+    int m = std::min(n, 3 * k + 6);
+    while (true) {
+        std::vector<double> th(m);
+        for (int j = 0; j < m; ++j) th[j] = kth_eig(a, b, n, j);
+        lam.clear();
+        int j = 0;
+        while (j < m && (int)lam.size() < k) {
+            int e = j + 1;
+            while (e < m && th[e] - th[e - 1] <= cluster) ++e;
+            // a cluster reaching the end of the computed values may continue
+            if (e == m && m < n) break;
+            bool keep = e - j >= 2;
+            if (!keep) {
+                keep = true;
+                if (n > 1) {
+                    const int c = sturm_count(ah, bh, n - 1, th[j] + cw) - sturm_count(ah, bh, n - 1, th[j] - cw);
+                    keep = c == 0;
+                }
+            }
+            if (keep) lam.push_back(th[j]);
+            j = e;
+        }
+        if ((int)lam.size() >= k || m >= n) break;
+        m = std::min(n, 2 * m);
+    }
+    vec.assign(lam.size(), std::vector<double>(n, 0.0));
+    for (size_t q = 0; q < lam.size(); ++q) {
+        std::vector<double>& z = vec[q];
+        for (int i = 0; i < n; ++i) z[i] = 1.0 + 0.01 * ((i * 7919 + 13 * (int)q) % 101);
+        for (int it = 0; it < 3; ++it) {
+            tri_solve(a, b, n, lam[q], z);
+            double nr = 0;
+            for (int i = 0; i < n; ++i) nr += z[i] * z[i];
+            nr = sqrt(nr);
+            if (nr == 0.0) break;
+            for (int i = 0; i < n; ++i) z[i] /= nr;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- driver
 template <int K>
 struct Lz {
@@ -353,6 +424,8 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     // FP32 vectors resolve eigenvalues to ~1e-7 relative: their phase runs at
     // a tolerance of at least 1e-6 and `tol` is the target of the refinement.
     const double tol = (K == 1 || K == 3) ? std::max(o->tol, 1e-6) : o->tol;
+    // unit roundoff of the vectors: copies of one eigenvalue agree to ~eps_v |T|
+    const double eps_v = (K == 1 || K == 3) ? 1.1920928955078125e-07 : 2.220446049250313e-16;
     ed_dtype vdt = o->dtype;
     for (int n = 0; n < max_it; ++n) {
         ed_status st = apply_launch(h, vdt, vec(n), w, 1, s);
@@ -381,7 +454,15 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         const bool breakdown = bh < 1e-13 * tnorm;
         const bool last = breakdown || n + 1 == max_it;
         if ((n + 1) % every == 0 || last) {
-            tri_eig(al, be, iters, n_eig + 1, lam, svec);
+            if (o->reorth) {
+                tri_eig(al, be, iters, n_eig + 1, lam, svec);
+            } else {
+                double tn = 0.0;
+                for (int i = 0; i < iters; ++i)
+                    tn = std::max(tn, fabs(al[i]) + (i > 0 ? be[i - 1] : 0.0) + (i + 1 < iters ? be[i] : 0.0));
+                tri_eig_filtered(al, be, iters, n_eig + 1, 100.0 * eps_v * tn, 1e3 * 2.220446049250313e-16 * tn, lam,
+                                 svec);
+            }
             // converged: for each wanted Ritz value, a small change since the
             // last check and a small residual bound r = beta |s_last| (the
             // eigenvalue error is at most min(r, r^2/gap)); with eigenvectors
@@ -420,8 +501,70 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         r.resid_bound[k] = be[iters - 1] * fabs(svec[k][iters - 1]);
         evals[k] = lam[k];
     }
-    // Ritz vectors (need stored Lanczos vectors)
+    // Ritz vectors: from the stored Lanczos vectors, or (plain recursion) by
+    // a second pass that regenerates v_1, v_2, ... from the same start with
+    // the recorded alpha, beta (the reductions are deterministic, so the
+    // vectors repeat bit for bit) and accumulates sum_j s_j v_j.
     const bool mixed = (K == 1 || K == 3);
+    const bool want_refine = mixed && o->refine > 0 && nk > 0;
+    constexpr int K64 = LV<K>::cplx ? 2 : 0;
+    using T64 = typename LV<K64>::T;
+    T64* y64 = nullptr;
+    std::vector<double> ssum(iters, 0.0);
+    for (int k = 0; k < nk; ++k)
+        for (int i = 0; i < iters; ++i) ssum[i] += svec[k][i];
+    if (want_refine) {
+        y64 = (T64*)z.get((size_t)D * sizeof(T64));
+        if (!y64) return fail(ED_ERR_NOMEM, "refinement workspace");
+    }
+    if (!o->reorth && nk > 0 && (evecs || want_refine)) {
+        const int nacc = evecs ? nk : 0;
+        std::vector<double2> alh(iters);
+        for (int j = 0; j < iters; ++j) alh[j] = make_double2(al[j], 0.0);
+        std::vector<double> sc((size_t)iters * (nacc + 1));
+        for (int j = 0; j < iters; ++j) {
+            for (int k = 0; k < nacc; ++k) sc[(size_t)j * (nacc + 1) + k] = svec[k][j];
+            sc[(size_t)j * (nacc + 1) + nacc] = ssum[j];
+        }
+        double2* al_d = (double2*)z.get((size_t)iters * sizeof(double2));
+        double* be_d = (double*)z.get((size_t)iters * sizeof(double));
+        double* sc_d = (double*)z.get(sc.size() * sizeof(double));
+        if (!al_d || !be_d || !sc_d) return fail(ED_ERR_NOMEM, "second-pass workspace");
+        ED_CUDA(cudaMemcpyAsync(al_d, alh.data(), (size_t)iters * sizeof(double2), cudaMemcpyHostToDevice, s));
+        ED_CUDA(cudaMemcpyAsync(be_d, be.data(), (size_t)iters * sizeof(double), cudaMemcpyHostToDevice, s));
+        ED_CUDA(cudaMemcpyAsync(sc_d, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (evecs) ED_CUDA(cudaMemsetAsync(evecs, 0, (size_t)nk * D * sizeof(T), s));
+        if (y64) ED_CUDA(cudaMemsetAsync(y64, 0, (size_t)D * sizeof(T64), s));
+        // v_1 exactly as in the first pass
+        if (start) ED_CUDA(cudaMemcpyAsync(vec(0), start, (size_t)D * sizeof(T), cudaMemcpyDeviceToDevice, s));
+        else if (h->basis->word == 8)
+            init_random<uint64_t, K><<<g, 256, 0, s>>>(vec(0), (const uint64_t*)h->basis->reps.p, D, o->seed);
+        else init_random<uint32_t, K><<<g, 256, 0, s>>>(vec(0), (const uint32_t*)h->basis->reps.p, D, o->seed);
+        dot(vec(0), 1, vec(0), coef);
+        sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
+        scale_by<K><<<g, 256, 0, s>>>(vec(0), vec(0), D, beta_d);
+        for (int j = 0; j < iters; ++j) {
+            const double* cj = sc_d + (size_t)j * (nacc + 1);
+            if (nacc) accumulate<K, T><<<g, 256, 0, s>>>((T*)evecs, D, nacc, cj, vec(j), D);
+            if (y64) accumulate<K, T64><<<g, 256, 0, s>>>(y64, D, 1, cj + nacc, vec(j), D);
+            if (j + 1 == iters) break;
+            ed_status st = apply_launch(h, vdt, vec(j), w, 1, s);
+            if (st != ED_OK) return st;
+            ++n_apply;
+            lanczos_axpy<K><<<g, 256, 0, s>>>(w, vec(j), j > 0 ? vec(j - 1) : nullptr, D, al_d + j,
+                                              j > 0 ? be_d + j - 1 : be_d);
+            scale_by<K><<<g, 256, 0, s>>>(vec(j + 1), w, D, be_d + j);
+        }
+        ED_CUDA(cudaGetLastError());
+        // the Lanczos vectors are not orthogonal: normalise each Ritz vector
+        for (int k = 0; k < nacc; ++k) {
+            T* ek = (T*)evecs + (int64_t)k * D;
+            dot(ek, 1, ek, coef);
+            sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
+            scale_by<K><<<g, 256, 0, s>>>(ek, ek, D, beta_d);
+        }
+        ED_CUDA(cudaStreamSynchronize(s));
+    }
     if (o->reorth && evecs) {
         double* sd = (double*)z.get((size_t)iters * sizeof(double));
         if (!sd) return fail(ED_ERR_NOMEM, "Ritz workspace");
@@ -435,18 +578,14 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     // Ritz vectors promoted to FP64 (the Krylov space of a start vector that
     // already overlaps the wanted eigenvectors converges in a few steps).
     if constexpr (K == 1 || K == 3) {
-        if (o->reorth && o->refine > 0 && nk > 0) {
-            constexpr int K64 = LV<K>::cplx ? 2 : 0;
-            using T64 = typename LV<K64>::T;
-            double* sd = (double*)z.get((size_t)iters * sizeof(double));
-            T64* y64 = (T64*)z.get((size_t)D * sizeof(T64));
-            if (!sd || !y64) return fail(ED_ERR_NOMEM, "refinement workspace");
-            std::vector<double> ssum(iters, 0.0);
-            for (int k = 0; k < nk; ++k)
-                for (int i = 0; i < iters; ++i) ssum[i] += svec[k][i];
-            ED_CUDA(cudaMemcpyAsync(sd, ssum.data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
-            combine<K, T64><<<g, 256, 0, s>>>(y64, V, D, iters, sd, D);
-            ED_CUDA(cudaStreamSynchronize(s));
+        if (want_refine) {
+            if (o->reorth) {
+                double* sd = (double*)z.get((size_t)iters * sizeof(double));
+                if (!sd) return fail(ED_ERR_NOMEM, "refinement workspace");
+                ED_CUDA(cudaMemcpyAsync(sd, ssum.data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
+                combine<K, T64><<<g, 256, 0, s>>>(y64, V, D, iters, sd, D);
+                ED_CUDA(cudaStreamSynchronize(s));
+            }
             ed_lanczos_opts o2 = *o;
             o2.dtype = K64 == 2 ? ED_C128 : ED_F64;
             o2.max_iter = std::max(o->refine, o->n_eig + 2);
@@ -486,3 +625,24 @@ ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double*
 }
 
 }  // namespace ed
+
+extern "C" ed_status ed_tridiag_eigs(const double* alpha, const double* beta, int32_t n, int32_t k, double eps_vectors,
+                                     int32_t filter, double* evals, int32_t* n_found) {
+    using namespace ed;
+    if (!alpha || (!beta && n > 1) || !evals || n < 1 || k < 1) return fail(ED_ERR_ARG, "bad argument");
+    std::vector<double> a(alpha, alpha + n), b(n, 0.0);
+    for (int i = 0; i + 1 < n; ++i) b[i] = beta[i];
+    std::vector<double> lam;
+    std::vector<std::vector<double>> vec;
+    if (filter) {
+        double tn = 0.0;
+        for (int i = 0; i < n; ++i)
+            tn = std::max(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
+        tri_eig_filtered(a, b, n, k, 100.0 * eps_vectors * tn, 1e3 * 2.220446049250313e-16 * tn, lam, vec);
+    } else {
+        tri_eig(a, b, n, k, lam, vec);
+    }
+    for (size_t i = 0; i < lam.size(); ++i) evals[i] = lam[i];
+    if (n_found) *n_found = (int32_t)lam.size();
+    return ED_OK;
+}

@@ -101,6 +101,9 @@ def lib():
         L.ed_batch_rows.argtypes = [c_vp, P(c_i64)]
         L.ed_apply_batch.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
         L.ed_batch_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp, P(c_i32)]
+        L.ed_apply_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp, P(c_i32)]
+        L.ed_apply_set_blocks.argtypes = [c_vp, ctypes.c_int, c_i32, c_i32]
+        L.ed_tridiag_eigs.argtypes = [P(c_dbl), P(c_dbl), c_i32, c_i32, c_dbl, c_i32, P(c_dbl), P(c_i32)]
         L.ed_batch_free.argtypes = [c_vp]
         L.ed_batch_free.restype = None
         L.ed_lanczos_batch.argtypes = [c_vp, P(ed_block_lanczos_opts), P(c_dbl), P(ed_block_lanczos_report), c_vp]
@@ -109,7 +112,8 @@ def lib():
         L.ed_last_error.restype = ctypes.c_char_p
         L.ed_version.restype = ctypes.c_char_p
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
-                  "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_lanczos"):
+                  "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
+                  "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -138,6 +142,19 @@ def _sector_struct(sector):
     s = ed_sector(int(sector.n_sites), int(sector.n_up), int(len(perm)), _ptr(perm, c_i32), _ptr(flip, c_u8),
                   _ptr(chi2, c_dbl), int(sector.n_sublat))
     return s, [perm, flip, chi2]
+
+
+def tridiag_eigs(alpha, beta, k, eps_vectors=2.0 ** -53, filter=True):
+    """ed_tridiag_eigs: lowest k eigenvalues of the T-matrix (host only)."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    if len(b) < max(0, len(a) - 1):
+        raise ValueError("beta needs n-1 entries")
+    out = np.zeros(k, np.float64)
+    nf = c_i32()
+    check(lib().ed_tridiag_eigs(_ptr(a, c_dbl), _ptr(b, c_dbl), len(a), k, eps_vectors, int(filter),
+                                _ptr(out, c_dbl), ctypes.byref(nf)))
+    return out[:nf.value]
 
 
 def sector_tables(sector) -> dict:
@@ -240,6 +257,22 @@ class Hamiltonian:
             stream = torch.cuda.current_stream(x.device)
         self.apply_ptr(dt, x.data_ptr(), y.data_ptr(), nvec, stream)
         return y
+
+    def autotune(self, x, y, stream=None):
+        """ed_apply_autotune on torch CUDA tensors shaped as for apply(); returns blocks per SM."""
+        import torch
+        dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
+        nvec = 1 if x.dim() == 1 else x.shape[0]
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        b = c_i32()
+        check(lib().ed_apply_autotune(self.handle, dt, x.data_ptr(), y.data_ptr(), nvec, _stream_handle(stream),
+                                      ctypes.byref(b)))
+        return int(b.value)
+
+    def set_blocks(self, dtype: int, nvec: int, blocks: int):
+        """ed_apply_set_blocks: resident blocks per SM for (dtype, nvec class); 0 = default."""
+        check(lib().ed_apply_set_blocks(self.handle, dtype, nvec, blocks))
 
     def counters(self, stream=None):
         g = c_i64()

@@ -247,3 +247,63 @@ def test_lanczos_eigenvectors(P):
         assert abs(np.linalg.norm(V[k]) - 1) < 1e-10
         assert abs(vals[k] - ref[k]) < 1e-10 * abs(ref[k])
     assert abs(np.vdot(V[0], V[1])) < 1e-8
+
+
+def _distinct(ref, k):
+    out = [ref[0]]
+    for e in ref[1:]:
+        if e - out[-1] > 1e-8:
+            out.append(e)
+    return out[:k]
+
+
+@pytest.mark.parametrize("name", ["chain16_nosym", "kagome12_E1", "triangular18_Gamma"])
+def test_lanczos_plain_recursion(P, name):
+    """The three-term recursion without reorthogonalisation (the memory regime of the
+    largest sectors): long enough for spurious copies of the lowest levels to appear;
+    after the Cullum-Willoughby filter the 4 lowest distinct levels match to 1e-10."""
+    p, reps, stab, H = _oracle(name)
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    k = 4
+    ev, rep = h.lanczos(n_eig=k, tol=1e-12, max_iter=min(800, b.dim), reorth=False)
+    ref = np.linalg.eigvalsh(H.toarray()) if H.shape[0] <= 6000 else oracle.lowest_eigs(H, 12)
+    distinct = _distinct(ref, k)
+    assert rep.converged
+    for i in range(len(distinct)):
+        assert abs(ev[i] - distinct[i]) <= 1e-10 * max(1.0, abs(distinct[i])), (i, ev, distinct)
+
+
+def test_lanczos_plain_recursion_eigenvectors(P):
+    """Ritz vectors of the plain recursion from its second pass (the vectors are
+    regenerated from the recorded alpha, beta)."""
+    import torch
+    p, reps, stab, H = _oracle("chain14_TRZ2_odd")
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    ev = torch.zeros((2, b.dim), dtype=torch.float64, device="cuda")
+    vals, rep = h.lanczos(n_eig=2, tol=1e-12, max_iter=300, reorth=False, evecs=ev)
+    V = ev.cpu().numpy()
+    ref = _distinct(np.linalg.eigvalsh(H.toarray()), 2)
+    assert rep.converged
+    for k in range(2):
+        r = H @ V[k] - vals[k] * V[k]
+        assert np.linalg.norm(r) <= 1e-5 * max(1.0, abs(vals[k]))
+        assert abs(np.linalg.norm(V[k]) - 1) < 1e-10
+        assert abs(vals[k] - ref[k]) < 1e-10 * abs(ref[k])
+    assert abs(np.vdot(V[0], V[1])) < 1e-5
+
+
+@pytest.mark.parametrize("name", ["square16_B1_odd", "kagome12_E1"])
+def test_lanczos_mixed_plain_recursion_refined(P, name):
+    """FP32 vectors without reorthogonalisation, refined in FP64 from the second-pass
+    Ritz vectors: the two lowest levels to 1e-10."""
+    p, reps, stab, H = _oracle(name)
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    dt = P.ED_F32 if h.is_real else P.ED_C64
+    ev, rep = h.lanczos(n_eig=2, tol=1e-10, max_iter=400, dtype=dt, reorth=False, refine=True)
+    ref = _distinct(np.linalg.eigvalsh(H.toarray()), 2)
+    for i in range(2):
+        assert abs(rep.ritz[i] - ref[i]) < 1e-5 * abs(ref[i])
+        assert abs(ev[i] - ref[i]) <= 1e-10 * abs(ref[i]), (i, ev[:2], ref, list(rep.ritz[:2]))

@@ -54,7 +54,8 @@ def _noalloc(P, sector, states_np):
 
 
 def test_noalloc_matches_allocating_entry_point_twice(P):
-    cases = [C.square32().sector, C.kagome([[2, 0], [0, 2]], 1.0, 0.2, 0.3, irrep="E1").sector]
+    # square32 with 8-site blocks: a 53 KB table image (16-site blocks need 1.7 MB)
+    cases = [C.square32(n_sublat=4).sector, C.kagome([[2, 0], [0, 2]], 1.0, 0.2, 0.3, irrep="E1").sector]
     rng = np.random.default_rng(11)
     for sector in cases:
         N = sector.n_sites
