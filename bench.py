@@ -58,18 +58,21 @@ def kernel_hash() -> str:
 
 
 def profiled_traffic(workload: str, dtype: str):
-    """DRAM bytes per launch of the H.x kernel from the committed ncu summary, if it matches this kernel."""
-    p = os.path.join(ROOT, "profiles", "hx_traffic.json")
+    """DRAM bytes per launch of the H.x kernel and ncu context counters from the
+    committed summary, if it was taken on these kernel sources; else (None, {})."""
+    p = os.path.join(ROOT, "profiles", "hx_traffic.txt")
     if not os.path.exists(p):
-        return None
-    try:
-        d = json.load(open(p))
-        e = d.get(f"{workload}:{dtype}")
-        if e and e.get("kernel_hash") == kernel_hash():
-            return float(e["dram_bytes_per_launch"])
-    except Exception:
-        return None
-    return None
+        return None, {}
+    for line in open(p):
+        f = line.split()
+        if not f or f[0].startswith("#") or f[0] != f"{workload}:{dtype}":
+            continue
+        kv = dict(x.split("=", 1) for x in f[1:] if "=" in x)
+        if kv.get("kernel_hash") != kernel_hash():
+            return None, {}
+        extra = {k: float(v) for k, v in kv.items() if k not in ("kernel_hash", "dram_bytes_per_launch")}
+        return float(kv["dram_bytes_per_launch"]), extra
+    return None, {}
 
 
 class ClockSampler:
@@ -177,7 +180,10 @@ def oracle_rate(problem, budget_s: float, cplx: bool):
 def batching_measurement(pkg, torch, stream):
     """Ground energy of every (k, rho_k) sector of the 24-site triangular torus
     (36 sectors, J1=1, J2=0.125, Sz=0): one Lanczos run per sector in sequence
-    against one block Lanczos run over all sectors (block 8, CUDA graph)."""
+    against one batched Lanczos run over all sectors (every step one persistent
+    H.x launch for all sectors, the step replayed as a CUDA graph), with one
+    vector per sector (plain recursion or full reorthogonalisation) and with a
+    block of 8 seeded Gaussian vectors."""
     from edinputs import configs as EC
     probs = EC.triangular24_sectors()
     bases = [pkg.Basis(p.sector, stream=stream) for p in probs]
@@ -193,18 +199,29 @@ def batching_measurement(pkg, torch, stream):
     torch.cuda.synchronize()
     t_seq = time.perf_counter() - t0
     batch = pkg.Batch(hs)
-    batch.lanczos(block=8, n_eig=1, tol=1e-10, max_iter=80, seed=3, use_graph=True, raise_on_nonconv=False)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ev, rep = batch.lanczos(block=8, n_eig=1, tol=1e-10, max_iter=80, seed=3, use_graph=True,
-                            raise_on_nonconv=False)
-    torch.cuda.synchronize()
-    t_bat = time.perf_counter() - t0
-    diff = max(abs(float(ev[s, 0]) - seq[s]) for s in range(len(hs)))
-    return {"workload": "triangular 24 sites, all 36 (k, rho_k) sectors, J2=0.125, Sz=0",
-            "total_dim": int(batch.total), "sequential_s": t_seq, "batched_graph_s": t_bat,
-            "speedup": t_seq / t_bat, "batched_iters": rep.iters, "converged_sectors": rep.converged_sectors,
-            "max_abs_E0_diff": diff, "E0_min": min(seq)}
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = {"workload": "triangular 24 sites, all 36 (k, rho_k) sectors, J2=0.125, Sz=0",
+           "total_dim": int(batch.total), "sequential_s": t_seq, "E0_min": min(seq)}
+    for blk, reorth in ((1, False), (1, True), (8, True)):
+        x = torch.zeros(blk * batch.total, dtype=torch.complex128, device=dev)
+        waves = batch.autotune(x, torch.empty_like(x), nvec=blk)
+        del x
+        max_it = 300 if blk == 1 else 80
+        if blk == 1:  # warm-up run (the block-8 run is long enough to carry its own set-up)
+            batch.lanczos(block=blk, n_eig=1, tol=1e-10, max_iter=max_it, seed=3, use_graph=True,
+                          raise_on_nonconv=False, reorth=reorth)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, rep = batch.lanczos(block=blk, n_eig=1, tol=1e-10, max_iter=max_it, seed=3, use_graph=True,
+                                raise_on_nonconv=False, reorth=reorth)
+        torch.cuda.synchronize()
+        t_bat = time.perf_counter() - t0
+        diff = max(abs(float(ev[s, 0]) - seq[s]) for s in range(len(hs)))
+        out[f"block{blk}_{'reorth' if reorth else 'plain'}"] = {
+            "batched_graph_s": t_bat, "speedup_vs_sequential": t_seq / t_bat, "iters": rep.iters,
+            "step_seconds": rep.step_seconds, "converged_sectors": rep.converged_sectors,
+            "max_abs_E0_diff": diff, "autotuned_waves": waves}
+    return out
 
 
 def main():
@@ -336,6 +353,7 @@ def main():
     per_launch = t_dev / args.steps / ws * ws  # seconds per launch on one GPU
     achieved = b_alg / (sum(ms) / 1e3 / args.steps) / 1e9
     peak, peak_kind = peaks()
+    traffic, ncu_ctx = profiled_traffic(args.workload, dtype)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
@@ -344,7 +362,7 @@ def main():
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "basis_build_s": round(t_basis, 4)},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(args.workload, dtype),
+                         "frac": achieved / peak, "traffic": traffic, "ncu_context": ncu_ctx,
                          "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": b_alg,
                          "gathers_per_launch": gathers, "incompatible_images_per_launch": skipped},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * x.element_size()),

@@ -70,7 +70,7 @@ HxArgs make_args(const ed_hamiltonian* h) {
     const uint8_t* dir = (const uint8_t*)b->limits.p;
     a.dir_base = (const uint32_t*)dir;
     a.dir_q = dir + b->dir_q_off();
-    a.limits = (const uint32_t*)(dir + b->dir_lim_off());
+    a.limits = (const uint2*)(dir + b->dir_lim_off());
     a.L = b->prefix_bits;
     a.S = 1 << b->ht.m;
     a.flips = (const FlipTerm*)h->d_flips.p;
@@ -109,7 +109,7 @@ ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void
     const uint8_t* dir = (const uint8_t*)b->limits.p;
     a.dir_base = (const uint32_t*)dir;
     a.dir_q = dir + b->dir_q_off();
-    a.limits = (const uint32_t*)(dir + b->dir_lim_off());
+    a.limits = (const uint2*)(dir + b->dir_lim_off());
     a.L = b->prefix_bits;
     a.S = 1 << b->ht.m;
     a.flips = (const FlipTerm*)h->d_flips.p;

@@ -331,7 +331,7 @@ template <typename W, bool CH, int K, int NV, int NS>
 __global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), NV, K))
     hx_batch_kernel(const HxArgs* __restrict__ desc, const int64_t* __restrict__ row_off, int n_sec, int64_t chunk,
                     const void* x, void* y, int nvec, const int* __restrict__ x_step, int64_t x_step_elems,
-                    unsigned long long* counters, int blocks) {
+                    unsigned long long* counters, int blocks, const int* __restrict__ active) {
     using T = typename Val<K>::T;
     // optional device-side block index: x advances by x_step_elems per step
     // (lets one captured launch serve every step of a block Lanczos run)
@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), NV, K))
             else hi = mid - 1;
         }
         for (int sct = lo; sct < n_sec && row_off[sct] < g1; ++sct) {
+            if (active && !active[sct]) continue;  // uniform over the block
             HxArgs a = desc[sct];
             a.nvec = nvec;
             a.blocks = blocks;
@@ -423,7 +424,7 @@ static ed_status launch_batch(const BatchLaunch& L, cudaStream_t s) {
     const int64_t chunk = std::max<int64_t>(1, (L.total_rows + grid - 1) / grid);
     const int64_t nblk = (L.total_rows + chunk - 1) / chunk;
     k<<<(unsigned)nblk, BLOCK, L.smem, s>>>(L.desc, L.row_off, L.n_sec, chunk, L.x, L.y, L.nvec, L.x_step,
-                                               L.x_step_elems, L.counters, L.blocks);
+                                               L.x_step_elems, L.counters, L.blocks, L.active);
     ED_CUDA(cudaGetLastError());
     return ED_OK;
 }

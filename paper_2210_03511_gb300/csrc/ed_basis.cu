@@ -192,7 +192,7 @@ __global__ void scan_tile_apply(const uint32_t* in, uint64_t n, const uint64_t* 
 // key = base_v + b; limits[key] = first index with state >= (v, b).
 template <typename W>
 __global__ void limits_kernel(const W* reps, uint64_t D, const uint32_t* seg_base, const uint8_t* seg_q,
-                              const uint64_t* v_lo, int S, int L, uint32_t* limits, uint64_t n_keys) {
+                              const uint64_t* v_lo, int S, int L, uint2* limits, uint64_t n_keys) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     for (uint64_t key = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; key < n_keys; key += stride) {
         // find v with seg_base[v] <= key < seg_base[v+1]
@@ -213,9 +213,22 @@ __global__ void limits_kernel(const W* reps, uint64_t D, const uint32_t* seg_bas
             if (reps[mid] < target) a0 = mid + 1;
             else a1 = mid;
         }
-        limits[key] = (uint32_t)a0;
+        limits[key].x = (uint32_t)a0;
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) limits[n_keys] = (uint32_t)D;
+    if (blockIdx.x == 0 && threadIdx.x == 0) limits[n_keys] = make_uint2((uint32_t)D, 0u);
+}
+
+// Fingerprints of the first (up to) 4 states of every bucket (after
+// limits_kernel has written all bucket starts).
+template <typename W>
+__global__ void fingerprint_kernel(const W* reps, uint2* limits, uint64_t n_keys) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t key = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; key < n_keys; key += stride) {
+        const uint32_t lo = limits[key].x, hi = limits[key + 1].x;
+        uint32_t f = 0;
+        for (uint32_t p = 0; p < 4 && lo + p < hi; ++p) f |= state_fp(reps[lo + p]) << (8 * p);
+        limits[key].y = f;
+    }
 }
 
 // ---------------------------------------------------------------- representatives of given states
@@ -527,7 +540,7 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
     seg_base[S] = (uint32_t)keys;
     b->prefix_bits = L;
     // device image of the Limits directory: [S+1] base, [S] q (padded), then limits
-    b->limits.bytes = (S + 1) * 4 + ((S + 15) & ~15) + (keys + 1) * 4;
+    b->limits.bytes = b->dir_lim_off() + (keys + 1) * 8;
     b->limits.p = b->alloc.get(b->limits.bytes, s);
     if (!b->limits.p) return fail(ED_ERR_NOMEM, "limits allocation");
     uint8_t* base = (uint8_t*)b->limits.p;
@@ -536,7 +549,7 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
     uint64_t* d_vlo = (uint64_t*)sc.get((S + 1) * 8);
     if (!d_vlo) return fail(ED_ERR_NOMEM, "limits scratch");
     ED_CUDA(cudaMemcpyAsync(d_vlo, v_lo.data(), (S + 1) * 8, cudaMemcpyHostToDevice, s));
-    uint32_t* d_lim = (uint32_t*)(base + (S + 1) * 4 + ((S + 15) & ~15));
+    uint2* d_lim = (uint2*)(base + b->dir_lim_off());
     const unsigned g = (unsigned)std::min<uint64_t>((keys + 255) / 256, (uint64_t)sms * 16);
     if (b->word == 8)
         limits_kernel<uint64_t><<<g, 256, 0, s>>>((const uint64_t*)b->reps.p, D, (const uint32_t*)base,
@@ -544,6 +557,9 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
     else
         limits_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, D, (const uint32_t*)base,
                                                   base + (S + 1) * 4, d_vlo, S, L, d_lim, keys);
+    ED_CUDA(cudaGetLastError());
+    if (b->word == 8) fingerprint_kernel<uint64_t><<<g, 256, 0, s>>>((const uint64_t*)b->reps.p, d_lim, keys);
+    else fingerprint_kernel<uint32_t><<<g, 256, 0, s>>>((const uint32_t*)b->reps.p, d_lim, keys);
     ED_CUDA(cudaGetLastError());
     ED_CUDA(cudaStreamSynchronize(s));
     b->n_keys = keys;

@@ -20,6 +20,7 @@
 #include <algorithm>
 #include <chrono>
 #include <complex>
+#include <thread>
 #include <vector>
 
 #include "ed_internal.h"
@@ -107,14 +108,18 @@ __global__ void bl_init(typename BV<K>::T* X, const HxArgs* desc, const int64_t*
 // X_j = X + j*xs (j = 0..*jmax, or 0 when jmax is null).  One block per
 // (tile, j); thread t handles pair (a, c) = (t / b % b, t % b) for rows
 // i = t / b^2 + m * (256 / b^2).
+// With local != 0 only the last two blocks take part (j = *jmax - 1 + blockIdx.y):
+// the plain three-term recursion.  Tiles of sectors with active[s] == 0 are skipped.
 template <int K>
 __global__ void __launch_bounds__(256) bl_gram(const typename BV<K>::T* X, int64_t xs, const int* jmax,
                                                const typename BV<K>::T* Y, const int64_t* tiles,
-                                               const int64_t* row_off, int b, double2* partial, int n_tiles) {
-    const int j = blockIdx.y;
-    if (jmax ? j > *jmax : j > 0) return;
+                                               const int64_t* row_off, int b, double2* partial, int n_tiles,
+                                               int local, const int* active) {
+    const int j = local ? *jmax - 1 + (int)blockIdx.y : (int)blockIdx.y;
+    if (j < 0 || (jmax ? j > *jmax : j > 0)) return;
     const int tile = blockIdx.x;
     const int s = (int)tiles[3 * tile];
+    if (!active[s]) return;  // a converged sector: its coefficients are not used
     const int64_t i0 = tiles[3 * tile + 1], i1 = tiles[3 * tile + 2];
     const int64_t D = row_off[s + 1] - row_off[s];
     const int64_t base = (int64_t)b * row_off[s];
@@ -147,12 +152,13 @@ __global__ void __launch_bounds__(256) bl_gram(const typename BV<K>::T* X, int64
 
 // C[s][j][a][c] = sum over the tiles of sector s (fixed order)
 __global__ void bl_reduce(const double2* partial, const int* tile_first, int n, int b, int n_tiles, const int* jmax,
-                          int jcap, double2* C) {
+                          int jcap, double2* C, int local) {
     const int s = blockIdx.x;
     const int bb = b * b;
     const int jm = jmax ? *jmax : 0;
-    for (int e = threadIdx.x; e < (jm + 1) * bb; e += blockDim.x) {
-        const int j = e / bb, ac = e % bb;
+    const int j0 = local ? max(0, jm - 1) : 0;
+    for (int e = threadIdx.x; e < (jm + 1 - j0) * bb; e += blockDim.x) {
+        const int j = j0 + e / bb, ac = e % bb;
         double2 sum = make_double2(0.0, 0.0);
         for (int tl = tile_first[s]; tl < tile_first[s + 1]; ++tl) {
             const double2 v = partial[((int64_t)j * n_tiles + tl) * bb + ac];
@@ -166,18 +172,21 @@ __global__ void bl_reduce(const double2* partial, const int* tile_first, int n, 
 // W[c][i] -= sum_{j <= jmax} sum_a X_j[a][i] C[s][j][a][c]
 template <int K>
 __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int64_t xs, const int* jmax,
-                          const double2* C, int jcap, const int64_t* row_off, int n, int b) {
+                          const double2* C, int jcap, const int64_t* row_off, int n, int b, int local,
+                          const int* active) {
     const int64_t total = row_off[n];
     const int jm = *jmax;
+    const int j0 = local ? max(0, jm - 1) : 0;
     const int bb = b * b;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
         const int s = sector_of(row_off, n, r);
+        if (!active[s]) continue;
         const int64_t i = r - row_off[s];
         const int64_t D = row_off[s + 1] - row_off[s];
         const int64_t base = (int64_t)b * row_off[s];
         double2 w[MAXB];
         for (int c = 0; c < b; ++c) w[c] = c_ld(W[base + (int64_t)c * D + i]);
-        for (int j = 0; j <= jm; ++j) {
+        for (int j = j0; j <= jm; ++j) {
             const double2* Cj = C + ((int64_t)s * jcap + j) * bb;
             for (int a = 0; a < b; ++a) {
                 const double2 x = c_ld(X[(int64_t)j * xs + base + (int64_t)a * D + i]);
@@ -195,9 +204,10 @@ __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int6
 // Per sector: G = R^H R (Cholesky, G from the W^H W gram), store R^{-1} and
 // accumulate Bacc = R * Bacc (Bacc starts as the identity).  A column whose
 // pivot collapses is dropped (R^{-1} column zero).
-__global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv, double2* Bacc, int first_pass) {
+__global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv, double2* Bacc, int first_pass,
+                        const int* active) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
-    if (s >= n) return;
+    if (s >= n || !active[s]) return;
     const int bb = b * b;
     const double2* g = G + (int64_t)s * jcap * bb;  // j = 0 slot
     double2 R[MAXB][MAXB], Ri[MAXB][MAXB];
@@ -259,12 +269,13 @@ __global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv,
 // Out[c][i] = sum_a W[a][i] Rinv[s][a][c]; Out may be W + (*kout)*os (device index) or W itself
 template <int K>
 __global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int64_t os, const int* kout, int kadd,
-                         const double2* Rinv, const int64_t* row_off, int n, int b) {
+                         const double2* Rinv, const int64_t* row_off, int n, int b, const int* active) {
     const int64_t total = row_off[n];
     typename BV<K>::T* out = Out + (kout ? (int64_t)(*kout + kadd) * os : 0);
     const int bb = b * b;
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
         const int s = sector_of(row_off, n, r);
+        if (!active[s]) continue;
         const int64_t i = r - row_off[s];
         const int64_t D = row_off[s + 1] - row_off[s];
         const int64_t base = (int64_t)b * row_off[s];
@@ -286,11 +297,12 @@ __global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int
 // Save A_k (= the j = k block of the first and second reorthogonalisation
 // coefficients, summed) and B_k (Bacc) into the per-step arrays; advance k.
 __global__ void bl_save(const double2* C1, const double2* C2, const double2* Bacc, int jcap, int n, int b, int* k,
-                        double2* Ahist, double2* Bhist, int kcap) {
+                        double2* Ahist, double2* Bhist, int kcap, const int* active) {
     const int kk = *k;
     const int bb = b * b;
     for (int e = threadIdx.x; e < n * bb; e += blockDim.x) {
         const int s = e / bb, ac = e % bb;
+        if (!active[s]) continue;
         const double2 a1 = C1[((int64_t)s * jcap + kk) * bb + ac], a2 = C2[((int64_t)s * jcap + kk) * bb + ac];
         Ahist[((int64_t)s * kcap + kk) * bb + ac] = make_double2(a1.x + a2.x, a1.y + a2.y);
         Bhist[((int64_t)s * kcap + kk) * bb + ac] = Bacc[(int64_t)s * bb + ac];
@@ -304,20 +316,28 @@ __global__ void bl_set_int(int* p, int v) { *p = v; }
 // ------------------------------------------------------------------ host: banded eigenvalues
 using cd = std::complex<double>;
 
-// number of eigenvalues of the Hermitian band matrix T (n x n, bandwidth bw,
-// dense storage) below x: negative pivots of the banded LDL^H of T - x I
-static int band_count(const std::vector<cd>& T, int n, int bw, double x) {
+// Hermitian band matrix in band storage: L[i*(bw+1) + k] = T[i][i-k], k = 0..bw.
+struct Band {
+    int n = 0, bw = 0;
+    std::vector<cd> L;
+    cd& at(int i, int k) { return L[(size_t)i * (bw + 1) + k]; }
+    cd get(int i, int k) const { return L[(size_t)i * (bw + 1) + k]; }
+};
+
+// number of eigenvalues of T below x: negative pivots of the banded LDL^H of T - x I
+static int band_count(const Band& T, double x) {
+    const int n = T.n, bw = T.bw;
     std::vector<cd> L((size_t)n * (bw + 1), cd(0));  // L[i][i-k] at i*(bw+1)+k
     std::vector<double> d(n, 0.0);
     int neg = 0;
     for (int j = 0; j < n; ++j) {
-        double dj = T[(size_t)j * n + j].real() - x;
+        double dj = T.get(j, 0).real() - x;
         for (int k = std::max(0, j - bw); k < j; ++k) dj -= std::norm(L[(size_t)j * (bw + 1) + (j - k)]) * d[k];
         if (dj == 0.0) dj = 1e-300;
         d[j] = dj;
         if (dj < 0) ++neg;
         for (int i = j + 1; i <= std::min(n - 1, j + bw); ++i) {
-            cd v = T[(size_t)i * n + j];
+            cd v = T.get(i, i - j);
             for (int k = std::max(0, i - bw); k < j; ++k)
                 v -= L[(size_t)i * (bw + 1) + (i - k)] * std::conj(L[(size_t)j * (bw + 1) + (j - k)]) * d[k];
             L[(size_t)i * (bw + 1) + (i - j)] = v / dj;
@@ -326,27 +346,41 @@ static int band_count(const std::vector<cd>& T, int n, int bw, double x) {
     return neg;
 }
 
-static std::vector<double> band_lowest(const std::vector<cd>& T, int n, int bw, int k) {
+// lowest m eigenvalues by bisection on the inertia
+static std::vector<double> band_lowest(const Band& T, int m) {
+    const int n = T.n, bw = T.bw;
     double lo = 1e300, hi = -1e300;
     for (int i = 0; i < n; ++i) {
         double r = 0;
-        for (int j = 0; j < n; ++j)
-            if (j != i) r += std::abs(T[(size_t)i * n + j]);
-        lo = std::min(lo, T[(size_t)i * n + i].real() - r);
-        hi = std::max(hi, T[(size_t)i * n + i].real() + r);
+        for (int k = 1; k <= bw && k <= i; ++k) r += std::abs(T.get(i, k));
+        for (int k = 1; k <= bw && i + k < n; ++k) r += std::abs(T.get(i + k, k));
+        lo = std::min(lo, T.get(i, 0).real() - r);
+        hi = std::max(hi, T.get(i, 0).real() + r);
     }
     std::vector<double> out;
-    for (int e = 0; e < std::min(k, n); ++e) {
+    for (int e = 0; e < std::min(m, n); ++e) {
         double a = lo, b2 = hi;
         for (int it = 0; it < 200; ++it) {
-            const double m = 0.5 * (a + b2);
-            if (m <= a || m >= b2) break;
-            if (band_count(T, n, bw, m) > e) b2 = m;
-            else a = m;
+            const double mid = 0.5 * (a + b2);
+            if (mid <= a || mid >= b2) break;
+            if (band_count(T, mid) > e) b2 = mid;
+            else a = mid;
         }
         out.push_back(0.5 * (a + b2));
     }
     return out;
+}
+
+// Lowest k eigenvalues of one sector's block-tridiagonal T.  With full
+// reorthogonalisation the plain values; the plain recursion (blocks of one:
+// a tridiagonal T with diagonal a1, off-diagonal b1) removes the spurious
+// copies of converged values as ed_lanczos does.
+static std::vector<double> sector_lowest(const Band& T, int k, bool filtered, const std::vector<double>& a1,
+                                         const std::vector<double>& b1) {
+    if (!filtered) return band_lowest(T, k);
+    std::vector<double> lam;
+    tridiag_lowest(a1, b1, T.n, k, true, 2.220446049250313e-16, lam);
+    return lam;
 }
 
 // ------------------------------------------------------------------ batch construction and apply
@@ -523,6 +557,7 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     using T = typename BV<K>::T;
     auto t0 = std::chrono::steady_clock::now();
     const int n = B->n, b = o->block, kcap = o->max_iter + 1, nt = B->n_tiles;
+    const int local = o->reorth ? 0 : 1;
     const int64_t tot = B->total;
     const int64_t bs = (int64_t)b * tot;  // elements per block vector
     const Alloc& A = *B->alloc;
@@ -553,8 +588,11 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     double2* Bhist = (double2*)get((size_t)n * kcap * bb * sizeof(double2));
     int* dk = (int*)get(16);
     int* tile_first = (int*)get((size_t)(n + 1) * 4);
-    if (!V || !W || !part || !C1 || !C2 || !G || !Rinv || !Bacc || !Ahist || !Bhist || !dk || !tile_first)
+    int* active = (int*)get((size_t)n * 4);  // 1 while a sector iterates; converged sectors drop out
+    if (!V || !W || !part || !C1 || !C2 || !G || !Rinv || !Bacc || !Ahist || !Bhist || !dk || !tile_first || !active)
         return fail(ED_ERR_NOMEM, "block Lanczos workspace");
+    std::vector<int> act_h(n, 1);
+    ED_CUDA(cudaMemcpy(active, act_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     {
         std::vector<int> tf(n + 1, 0);
         for (int t = 0, s = 0; s <= n; ++s) {
@@ -582,11 +620,11 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     bl_init<K><<<g, 256, 0, s>>>(W, desc, ro, n, b, o->seed, B->w8 ? 8 : 4);
     auto cholqr = [&](T* src, T* dst, int64_t dst_os, const int* kout, int kadd) {
         for (int pass = 0; pass < 2; ++pass) {
-            bl_gram<K><<<dim3(nt, 1), 256, 0, s>>>(src, 0, nullptr, src, tiles, ro, b, part, nt);
-            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, nullptr, kcap, G);
-            bl_chol<<<(n + 63) / 64, 64, 0, s>>>(G, kcap, n, b, Rinv, Bacc, pass == 0);
+            bl_gram<K><<<dim3(nt, 1), 256, 0, s>>>(src, 0, nullptr, src, tiles, ro, b, part, nt, 0, active);
+            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, nullptr, kcap, G, 0);
+            bl_chol<<<(n + 63) / 64, 64, 0, s>>>(G, kcap, n, b, Rinv, Bacc, pass == 0, active);
             bl_scale<K><<<g, 256, 0, s>>>(src, pass == 0 ? src : dst, dst_os, pass == 0 ? nullptr : kout, kadd, Rinv,
-                                          ro, n, b);
+                                          ro, n, b, active);
         }
     };
     bl_set_int<<<1, 1, 0, s>>>(dk, 0);
@@ -594,6 +632,7 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     ED_CUDA(cudaGetLastError());
     // one step, all sectors
     BatchLaunch L = make_launch(B, o->dtype, V, W, b);
+    L.active = active;
     L.x_step = dk;
     L.x_step_elems = bs;
     auto step = [&]() -> ed_status {
@@ -601,12 +640,12 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         if (st != ED_OK) return st;
         for (int pass = 0; pass < 2; ++pass) {
             double2* Cp = pass == 0 ? C1 : C2;
-            bl_gram<K><<<dim3(nt, kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt);
-            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp);
-            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b);
+            bl_gram<K><<<dim3(nt, local ? 2 : kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt, local, active);
+            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp, local);
+            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, local, active);
         }
         cholqr(W, V, bs, dk, 1);  // V_{k+1} = W R^-1, B_k accumulated in Bacc
-        bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap);
+        bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
         return ED_OK;
     };
     // load every kernel of the step once outside any capture; the values this
@@ -614,8 +653,8 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     {
         ed_status st = apply_batch_launch(L, s);
         if (st != ED_OK) return st;
-        bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b);
-        bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap);
+        bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b, local, active);
+        bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
         bl_set_int<<<1, 1, 0, s>>>(dk, 0);
         ED_CUDA(cudaGetLastError());
         ED_CUDA(cudaStreamSynchronize(s));
@@ -661,44 +700,55 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         if ((k + 1) % every && !last) continue;
         ED_CUDA(cudaMemcpy(Ah.data(), Ahist, Ah.size() * sizeof(double2), cudaMemcpyDeviceToHost));
         ED_CUDA(cudaMemcpy(Bh.data(), Bhist, Bh.size() * sizeof(double2), cudaMemcpyDeviceToHost));
-        // T (iters*b square): diag blocks A_j, block (j+1, j) = B_j.  Columns of
-        // V_{j+1} that collapsed in the Cholesky QR (zero diagonal of B_j, a
-        // sector smaller than the Krylov space) are left out of T.
+        // T (iters*b square): diag blocks A_j, block (j+1, j) = B_j, in band
+        // storage.  Columns of V_{j+1} that collapsed in the Cholesky QR (zero
+        // diagonal of B_j, a sector smaller than the Krylov space) are left out.
         const int nt2 = iters * b;
-        int nconv = 0;
-        for (int sct = 0; sct < n; ++sct) {
-            std::vector<cd> Tf((size_t)nt2 * nt2, cd(0));
+        auto check_sector = [&](int sct) {
+            if (!act_h[sct]) return;  // converged earlier: its values stay
             std::vector<char> valid(nt2, 1);
             double tn = 0.0;
             for (int j = 0; j < iters; ++j) {
                 const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
+                for (int r = 0; r < b; ++r) tn = std::max(tn, std::abs(cd(Aj[r * b + r].x, Aj[r * b + r].y)));
+            }
+            for (int j = 0; j + 1 < iters; ++j) {
+                const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
                 for (int r = 0; r < b; ++r)
-                    for (int c = 0; c < b; ++c) {
-                        // Hermitian part of A_j
-                        const cd v = 0.5 * (cd(Aj[r * b + c].x, Aj[r * b + c].y) + std::conj(cd(Aj[c * b + r].x, Aj[c * b + r].y)));
-                        Tf[(size_t)(j * b + r) * nt2 + j * b + c] = v;
-                        tn = std::max(tn, std::abs(v));
-                    }
+                    if (!(Bj[r * b + r].x > 1e-12 * std::max(tn, 1e-300))) valid[(j + 1) * b + r] = 0;
+            }
+            std::vector<int> pos(nt2, -1);
+            int nk2 = 0;
+            for (int i = 0; i < nt2; ++i)
+                if (valid[i]) pos[i] = nk2++;
+            Band T;
+            T.n = nk2;
+            T.bw = 2 * b - 1;
+            T.L.assign((size_t)nk2 * (T.bw + 1), cd(0));
+            auto put = [&](int r, int c, cd v) {  // lower-triangle entry (r >= c) of the full index space
+                if (pos[r] < 0 || pos[c] < 0) return;
+                T.at(pos[r], pos[r] - pos[c]) = v;
+            };
+            for (int j = 0; j < iters; ++j) {
+                const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
+                for (int r = 0; r < b; ++r)
+                    for (int c = 0; c <= r; ++c)  // Hermitian part of A_j
+                        put(j * b + r, j * b + c,
+                            0.5 * (cd(Aj[r * b + c].x, Aj[r * b + c].y) + std::conj(cd(Aj[c * b + r].x, Aj[c * b + r].y))));
                 if (j + 1 < iters) {
                     const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
-                    for (int r = 0; r < b; ++r) {
-                        if (!(Bj[r * b + r].x > 1e-12 * std::max(tn, 1e-300))) valid[(j + 1) * b + r] = 0;
-                        for (int c = 0; c < b; ++c) {
-                            const cd v(Bj[r * b + c].x, Bj[r * b + c].y);
-                            Tf[(size_t)((j + 1) * b + r) * nt2 + j * b + c] = v;
-                            Tf[(size_t)(j * b + c) * nt2 + (j + 1) * b + r] = std::conj(v);
-                        }
-                    }
+                    for (int r = 0; r < b; ++r)
+                        for (int c = 0; c < b; ++c) put((j + 1) * b + r, j * b + c, cd(Bj[r * b + c].x, Bj[r * b + c].y));
                 }
             }
-            std::vector<int> keep;
-            for (int i = 0; i < nt2; ++i)
-                if (valid[i]) keep.push_back(i);
-            const int nk2 = (int)keep.size();
-            std::vector<cd> Tm((size_t)nk2 * nk2);
-            for (int r = 0; r < nk2; ++r)
-                for (int c = 0; c < nk2; ++c) Tm[(size_t)r * nk2 + c] = Tf[(size_t)keep[r] * nt2 + keep[c]];
-            std::vector<double> lam = band_lowest(Tm, nk2, 2 * b - 1, n_eig);
+            std::vector<double> a1, b1;
+            if (local) {  // blocks of one
+                a1.resize(nk2);
+                b1.assign(nk2, 0.0);
+                for (int i = 0; i < nk2; ++i) a1[i] = T.get(i, 0).real();
+                for (int i = 0; i + 1 < nk2; ++i) b1[i] = std::abs(T.get(i + 1, 1));
+            }
+            const std::vector<double> lam = sector_lowest(T, n_eig, local, a1, b1);
             bool ok = (int)lam.size() == n_eig;
             for (int e = 0; e < (int)lam.size(); ++e) {
                 cur[sct][e] = lam[e];
@@ -706,9 +756,30 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
                 if (fabs(lam[e] - prev[sct][e]) > o->tol * sc) ok = false;
             }
             steady[sct] = ok ? steady[sct] + 1 : 0;
-            if (steady[sct] >= 2) ++nconv;
             prev[sct] = cur[sct];
+        };
+        {
+            // sectors are independent: spread them over the host's cores
+            const int nth = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            for (int t = 1; t < nth; ++t)
+                pool.emplace_back([&, t]() {
+                    for (int sct = t; sct < n; sct += nth) check_sector(sct);
+                });
+            for (int sct = 0; sct < n; sct += nth) check_sector(sct);
+            for (auto& th : pool) th.join();
         }
+        int nconv = 0;
+        bool changed = false;
+        for (int sct = 0; sct < n; ++sct)
+            if (steady[sct] >= 2) {
+                ++nconv;
+                if (act_h[sct]) {
+                    act_h[sct] = 0;  // converged: later steps skip its rows
+                    changed = true;
+                }
+            }
+        if (changed && nconv < n) ED_CUDA(cudaMemcpy(active, act_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
         conv_all = nconv;
         if (nconv == n || last) break;
     }
@@ -733,6 +804,9 @@ extern "C" ed_status ed_lanczos_batch(const ed_batch* B, const ed_block_lanczos_
     if (o->block < 1 || o->block > 8) return fail(ED_ERR_ARG, "block size out of range [1,8]");
     if (o->n_eig < 1 || o->n_eig > 64) return fail(ED_ERR_ARG, "n_eig out of range");
     if (o->max_iter < 2 || o->max_iter > 400) return fail(ED_ERR_ARG, "max_iter out of range [2,400]");
+    // blocks of several vectors keep full reorthogonalisation: without it, the
+    // copies of converged values cannot be told from genuine multiplicities
+    if (!o->reorth && o->block != 1) return fail(ED_ERR_ARG, "the plain recursion needs block = 1");
     if (o->dtype == ED_F64) {
         if (!B->all_real) return fail(ED_ERR_ARG, "a complex sector needs ED_C128");
         return block_lanczos<0>(B, o, evals, rep, (cudaStream_t)stream);

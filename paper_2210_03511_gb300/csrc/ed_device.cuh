@@ -367,20 +367,47 @@ ED_HD bool is_rep(W s, const TabView<CHUNKED>& t, int& nstab, bool& compat) {
     return true;
 }
 
+ED_HD int popc32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+    return __popc(v);
+#else
+    return __builtin_popcount(v);
+#endif
+}
+
+// 8-bit fingerprint of a state (top byte of a Fibonacci hash, so it depends
+// on every bit).
+template <typename W>
+ED_HD uint32_t state_fp(W r) {
+    return (uint32_t)(((uint64_t)r * 0x9E3779B97F4A7C15ull) >> 56);
+}
+
 // Index of representative r (section "Distributed and hybrid memory
 // parallelization": Basis + Limits, then binary search).  Limits is two-level:
 // the top sublattice block value v selects a directory entry (base_v, q_v),
-// the next q_v bits select a bucket [limits[key], limits[key+1]) of the
-// ascending basis.  Returns -1 if r is absent.
+// the next q_v bits select a bucket [limits[key].x, limits[key+1].x) of the
+// ascending basis.  A bucket of at most 4 states also carries their 8-bit
+// fingerprints: r is a compatible representative of this sector, so it is in
+// its bucket, and a fingerprint that matches exactly one state of the bucket
+// gives its position without reading the basis.  Otherwise (larger bucket, or
+// a fingerprint shared within the bucket) binary search; -1 if r is absent.
 template <typename W>
 ED_HD int64_t find_index(W r, const W* __restrict__ reps, const uint32_t* __restrict__ dir_base,
-                                              const uint8_t* __restrict__ dir_q, const uint32_t* __restrict__ limits,
-                                              int L) {
+                         const uint8_t* __restrict__ dir_q, const uint2* __restrict__ limits, int L) {
     const uint32_t top = (uint32_t)(r >> L);
     const int q = dir_q[top];
     const W low = L ? (r & (((W)1 << L) - 1)) : (W)0;
     const uint32_t key = dir_base[top] + (q ? (uint32_t)(low >> (L - q)) : 0u);
-    uint32_t lo = ld_ro(limits + key), hi = ld_ro(limits + key + 1);
+    const uint2 e = ld_ro(limits + key);
+    uint32_t lo = e.x, hi = ld_ro((const uint32_t*)(limits + key + 1));
+    const uint32_t n = hi - lo;
+    if (n <= 4u) {
+        // bytes of e.y equal to the fingerprint: 0x80 in each zero byte of x
+        const uint32_t x = e.y ^ (state_fp(r) * 0x01010101u);
+        uint32_t z = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
+        z &= n == 4u ? 0xFFFFFFFFu : ((1u << (8u * n)) - 1u);
+        if (popc32(z) == 1) return (int64_t)lo + (ctz32(z) >> 3);
+    }
     const uint32_t end = hi;
     while (lo < hi) {
         const uint32_t mid = (lo + hi) >> 1;

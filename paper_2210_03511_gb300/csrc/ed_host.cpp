@@ -588,7 +588,6 @@ ed_status ed_lanczos(const ed_hamiltonian* h, const ed_lanczos_opts* opts, doubl
     if (opts->max_iter < 1 || opts->max_iter > 2000) return fail(ED_ERR_ARG, "max_iter out of range [1,2000]");
     if ((opts->dtype == ED_F64 || opts->dtype == ED_F32) && !h->is_real)
         return fail(ED_ERR_ARG, "complex Hamiltonian or characters need a complex dtype");
-    if (evecs && !opts->reorth) return fail(ED_ERR_ARG, "eigenvectors need reorth=1 (stored Lanczos vectors)");
     return lanczos_run(h, opts, evals, evecs, report, (cudaStream_t)stream);
 }
 

@@ -123,12 +123,13 @@ struct ed_basis {
     // Two-level Limits directory, one device allocation:
     //   base[S+1] (uint32): first key of top-block value v
     //   q[S] (uint8, padded to 16 bytes): bucket bits used below the top block for v
-    //   limits[n_keys+1] (uint32): first basis index of each bucket
+    //   limits[n_keys+1] (uint2, 16-byte aligned): .x first basis index of the
+    //     bucket, .y byte p = fingerprint state_fp() of its state p < 4
     ed::DevBuf limits;
     uint64_t n_keys = 0;
     int device = 0;
     size_t dir_q_off() const { return (size_t)((1 << ht.m) + 1) * 4; }
-    size_t dir_lim_off() const { return dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15); }
+    size_t dir_lim_off() const { return (dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15) + 15) & ~(size_t)15; }
 };
 
 struct ed_hamiltonian {
@@ -157,7 +158,7 @@ struct HxArgs {
     const uint16_t* stab;
     const uint32_t* dir_base;
     const uint8_t* dir_q;
-    const uint32_t* limits;
+    const uint2* limits;
     int L, S;
     int blocks;                   // resident blocks per SM the launch is sized for (drives the staging plan)
     const FlipTerm* flips;
@@ -193,6 +194,7 @@ struct BatchLaunch {
     unsigned long long* counters;
     int waves;                 // grid = SMs x resident blocks x waves
     int blocks;                // resident blocks per SM (staging plan of every sector)
+    const int* active;         // device [n_sec]: rows of sectors with 0 are skipped (null: all)
 };
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s);
 size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec, int blocks);
@@ -208,6 +210,8 @@ ed_status representatives_static(const ed_sector* sector, const uint64_t* states
 // implemented in ed_apply.cu
 ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
 // implemented in ed_lanczos.cu
+void tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b, int n, int k, bool filter,
+                    double eps_v, std::vector<double>& lam);
 ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
                       ed_lanczos_report* rep, cudaStream_t s);
 }  // namespace ed

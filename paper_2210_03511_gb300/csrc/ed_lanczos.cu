@@ -353,6 +353,22 @@ static void tri_eig_filtered(const std::vector<double>& a, const std::vector<dou
     }
 }
 
+// Lowest k eigenvalues of the tridiagonal T (diagonal a, off-diagonal b),
+// optionally with the spurious-value filter (eps_v: unit roundoff of the
+// Lanczos vectors); shared with the batched solver and ed_tridiag_eigs.
+void tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b, int n, int k, bool filter,
+                    double eps_v, std::vector<double>& lam) {
+    std::vector<std::vector<double>> vec;
+    if (!filter) {
+        tri_eig(a, b, n, k, lam, vec);
+        return;
+    }
+    double tn = 0.0;
+    for (int i = 0; i < n; ++i)
+        tn = std::max(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
+    tri_eig_filtered(a, b, n, k, 100.0 * eps_v * tn, 1e3 * 2.220446049250313e-16 * tn, lam, vec);
+}
+
 // ---------------------------------------------------------------- driver
 template <int K>
 struct Lz {
@@ -633,15 +649,7 @@ extern "C" ed_status ed_tridiag_eigs(const double* alpha, const double* beta, in
     std::vector<double> a(alpha, alpha + n), b(n, 0.0);
     for (int i = 0; i + 1 < n; ++i) b[i] = beta[i];
     std::vector<double> lam;
-    std::vector<std::vector<double>> vec;
-    if (filter) {
-        double tn = 0.0;
-        for (int i = 0; i < n; ++i)
-            tn = std::max(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
-        tri_eig_filtered(a, b, n, k, 100.0 * eps_vectors * tn, 1e3 * 2.220446049250313e-16 * tn, lam, vec);
-    } else {
-        tri_eig(a, b, n, k, lam, vec);
-    }
+    tridiag_lowest(a, b, n, k, filter != 0, eps_vectors, lam);
     for (size_t i = 0; i < lam.size(); ++i) evals[i] = lam[i];
     if (n_found) *n_found = (int32_t)lam.size();
     return ED_OK;

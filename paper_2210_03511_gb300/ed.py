@@ -58,7 +58,7 @@ class ed_lanczos_opts(ctypes.Structure):
 
 class ed_block_lanczos_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("block", c_i32), ("n_eig", c_i32), ("tol", c_dbl), ("max_iter", c_i32),
-                ("seed", c_u64), ("use_graph", c_i32), ("check_every", c_i32)]
+                ("seed", c_u64), ("use_graph", c_i32), ("check_every", c_i32), ("reorth", c_i32)]
 
 
 class ed_block_lanczos_report(ctypes.Structure):
@@ -353,10 +353,10 @@ class Batch:
         return int(w.value)
 
     def lanczos(self, block=8, n_eig=3, tol=1e-10, max_iter=60, seed=1, use_graph=True, check_every=1,
-                dtype=None, raise_on_nonconv=True):
+                dtype=None, raise_on_nonconv=True, reorth=True):
         if dtype is None:
             dtype = ED_F64 if self.is_real else ED_C128
-        o = ed_block_lanczos_opts(dtype, block, n_eig, tol, max_iter, seed, int(use_graph), check_every)
+        o = ed_block_lanczos_opts(dtype, block, n_eig, tol, max_iter, seed, int(use_graph), check_every, int(reorth))
         ev = np.zeros(self.n * n_eig, np.float64)
         rep = ed_block_lanczos_report()
         st = lib().ed_lanczos_batch(self.handle, ctypes.byref(o), _ptr(ev, c_dbl), ctypes.byref(rep), None)

@@ -76,3 +76,29 @@ def test_block_lanczos_all_sectors(P, tri12, use_graph):
     for s, p in enumerate(tri12):
         ref = np.linalg.eigvalsh(oracle.csr(p).toarray())[:n_eig]
         assert np.allclose(ev[s, :len(ref)], ref, rtol=0, atol=1e-10 * max(1.0, abs(ref[0]))), (s, ev[s], ref)
+
+
+def test_block_lanczos_plain_recursion_needs_block_one(P, tri12):
+    """Without reorthogonalisation the batched solver takes one vector per sector only."""
+    bases = [P.Basis(p.sector) for p in tri12[:3]]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12[:3])]
+    batch = P.Batch(hs)
+    with pytest.raises(P.EdError) as e:
+        batch.lanczos(block=4, n_eig=2, tol=1e-10, max_iter=40, reorth=False)
+    assert e.value.name == "ED_ERR_ARG"
+
+
+@pytest.mark.parametrize("reorth", [True, False])
+def test_batched_single_vector_lanczos(P, tri12, reorth):
+    """Block size 1: one Lanczos vector per sector, all sectors advanced by one graph
+    launch per step (converged sectors drop out), with full reorthogonalisation or the
+    plain recursion (spurious copies filtered); each sector's ground level to 1e-10 (a
+    single vector sees each degenerate level once, so only the lowest is compared)."""
+    bases = [P.Basis(p.sector) for p in tri12]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12)]
+    batch = P.Batch(hs)
+    ev, rep = batch.lanczos(block=1, n_eig=1, tol=1e-12, max_iter=300, seed=7, use_graph=True, reorth=reorth)
+    assert rep.converged_sectors == len(tri12) and rep.used_graph == 1
+    for s, p in enumerate(tri12):
+        e0 = np.linalg.eigvalsh(oracle.csr(p).toarray())[0]
+        assert abs(ev[s, 0] - e0) <= 1e-10 * max(1.0, abs(e0)), (s, ev[s, 0], e0)
