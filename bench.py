@@ -364,7 +364,11 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "ncu_context": ncu_ctx,
                          "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": b_alg,
-                         "gathers_per_launch": gathers, "incompatible_images_per_launch": skipped},
+                         "gathers_per_launch": gathers, "incompatible_images_per_launch": skipped,
+                         # the DRAM bytes the launch really moves (ncu, same kernel sources) over the
+                         # same launch time: each gather costs whole random sectors, not s_x bytes
+                         "dram_achieved": (traffic / (sum(ms) / 1e3 / args.steps) / 1e9) if traffic else None,
+                         "dram_frac": (traffic / (sum(ms) / 1e3 / args.steps) / 1e9 / peak) if traffic else None},
             "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * x.element_size()),
                     "d2h_bytes_per_step": int(y.numel() * y.element_size())},
             "gpu_launches": args.steps,
@@ -372,11 +376,14 @@ def main():
             "wall_s_timed_region": wall}
     if not args.no_lanczos and rank == 0:
         lz = {}
-        # full reorthogonalisation while 300 stored FP64 vectors take under 100 GB, else
-        # the plain recursion (ghost-filtered, Ritz vectors from a second pass)
-        reorth = 300 * D * (16 if not real else 8) < 100e9
+        # full reorthogonalisation while 300 stored vectors of the run's own dtype take
+        # under 180 GB of HBM, else the plain recursion (ghost-filtered, Ritz vectors
+        # from a second pass): FP32 vectors halve that memory, one of the gains of
+        # the mixed-precision run
         for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
                                  ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
+            s_vec = {pkg.ED_F64: 8, pkg.ED_F32: 4, pkg.ED_C128: 16, pkg.ED_C64: 8}[dt]
+            reorth = 300 * D * s_vec < 180e9
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=300, dtype=dt, reorth=reorth,
