@@ -277,6 +277,18 @@ typedef struct {
 ed_status ed_lanczos(const ed_hamiltonian* h, const ed_lanczos_opts* opts, double* evals, void* evecs,
                      ed_lanczos_report* report, ed_stream stream);
 
+/* ed_expectation -- <x_v|H|x_v> and <x_v|x_v> for nvec (1..8) DEVICE vectors
+ * laid out as for ed_apply, with FP64 reductions: out (HOST) [nvec][3] =
+ * (Re <x|Hx>, Im <x|Hx>, <x|x>).  One ed_apply into a workspace from the
+ * basis's allocator.  With H the orbit average of a bond operator,
+ * (1/|orbit|) sum over the bonds {i', j'} of the symmetry orbit of {i, j} of
+ * S_i'.S_j', this gives the spin correlation <S_i.S_j> of a state of the
+ * sector (the correlations behind the static structure factor, Eq.
+ * structurefactor): <psi|g O g^-1|psi> = <psi|O|psi> for a state of a
+ * one-dimensional irrep.  Synchronous on `stream`. */
+ed_status ed_expectation(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t nvec, ed_stream stream,
+                         double* out);
+
 /* Lowest k eigenvalues of a Lanczos T-matrix (Eq. tmatrix: diagonal alpha[n],
  * off-diagonal beta[n-1], HOST arrays) by Sturm bisection in FP64, the solver
  * ed_lanczos uses.  filter = 1 applies its treatment of the plain recursion:

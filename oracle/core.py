@@ -19,7 +19,9 @@ Large-Scale Exact Diagonalization" and the sections it builds on):
   * sector dimensions by the character formula (Eq. characterformula) --
     `sector_dim_formula`;
   * eigenvalues: dense LAPACK or ARPACK on the CSR -- `lowest_eigs`;
-  * matrix-free sampled rows with keyed-random x -- `rows`.
+  * matrix-free sampled rows with keyed-random x -- `rows`;
+  * spin correlations <S_i.S_j> of a symmetric-basis state, written out in the
+    product basis (Eq. structurefactor) -- `correlation_matrix`.
 """
 from __future__ import annotations
 
@@ -253,6 +255,43 @@ def projector_matrix(sector, states: np.ndarray) -> tuple[np.ndarray, list[int]]
         ph = V[index[m], c]
         V[:, c] *= np.conj(ph) / abs(ph)
     return V, kept
+
+
+def correlation_matrix(sector, psi: np.ndarray) -> np.ndarray:
+    """C[i, j] = <phi|S_i . S_j|phi> / <phi|phi> for the state phi = sum_c psi_c v_c
+    written out in the fixed-Sz product basis (v_c the explicit projections of
+    `projector_matrix`, in basis order), each S_i . S_j applied through the
+    4x4 matrix of its definition (ops.bond_matrix).  The spin correlation of
+    Eq. structurefactor.  N <= 20."""
+    N = sec_N(sector)
+    states = sz_states(N, sector.n_up)
+    V, kept = projector_matrix(sector, states)
+    assert V.shape[1] == len(psi)
+    phi = V @ np.asarray(psi, dtype=complex)
+    nrm = float(np.real(np.vdot(phi, phi)))
+    M = ops.bond_matrix()
+    idx = {int(st): k for k, st in enumerate(states)}
+    C = np.zeros((N, N))
+    for i in range(N):
+        for j in range(N):
+            bi, bj = N - 1 - i, N - 1 - j
+            out = np.zeros_like(phi)
+            for k, st in enumerate(states):
+                st = int(st)
+                if i == j:
+                    out[k] += 0.75 * phi[k]     # S_i . S_i = s(s+1) = 3/4
+                    continue
+                a = 2 * ((st >> bi) & 1) + ((st >> bj) & 1)
+                for ap in range(4):
+                    m = M[ap, a]
+                    if m == 0:
+                        continue
+                    t = st & ~((1 << bi) | (1 << bj))
+                    t |= ((ap >> 1) & 1) << bi
+                    t |= (ap & 1) << bj
+                    out[idx[t]] += m * phi[k]
+            C[i, j] = float(np.real(np.vdot(phi, out))) / nrm
+    return C
 
 
 def sec_N(sector) -> int:

@@ -393,6 +393,10 @@ struct Lz {
 };
 
 static int dtype_kind(ed_dtype d) { return d == ED_F64 ? 0 : d == ED_F32 ? 1 : d == ED_C128 ? 2 : 3; }
+template <int K>
+static ed_dtype dtype_of() {
+    return K == 0 ? ED_F64 : K == 1 ? ED_F32 : K == 2 ? ED_C128 : ED_C64;
+}
 
 template <int K>
 static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
@@ -640,7 +644,59 @@ ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double*
     }
 }
 
+template <int K>
+static ed_status expectation_kind(const ed_hamiltonian* h, const void* x, int nvec, cudaStream_t s, double* out) {
+    using T = typename LV<K>::T;
+    Lz<K> z;
+    z.h = h;
+    z.b = h->basis;
+    z.s = s;
+    z.D = h->basis->dim;
+    ED_CUDA(cudaDeviceGetAttribute(&z.sms, cudaDevAttrMultiProcessorCount, h->basis->device));
+    const int64_t D = z.D;
+    z.nb = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (D + 4095) / 4096));
+    T* y = (T*)z.get((size_t)nvec * D * sizeof(T));
+    double2* partial = (double2*)z.get((size_t)z.nb * sizeof(double2));
+    double2* res = (double2*)z.get((size_t)2 * nvec * sizeof(double2));
+    if (!y || !partial || !res) return fail(ED_ERR_NOMEM, "expectation workspace");
+    const ed_status st = apply_launch(h, dtype_of<K>(), x, y, nvec, s);
+    if (st != ED_OK) return st;
+    const T* xv = (const T*)x;
+    for (int v = 0; v < nvec; ++v) {
+        multi_dot<K><<<dim3(z.nb, 1), 256, 0, s>>>(xv + (int64_t)v * D, D, y + (int64_t)v * D, D, partial);
+        reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, res + 2 * v);
+        multi_dot<K><<<dim3(z.nb, 1), 256, 0, s>>>(xv + (int64_t)v * D, D, xv + (int64_t)v * D, D, partial);
+        reduce_partials<<<1, 256, 0, s>>>(partial, z.nb, 1, res + 2 * v + 1);
+    }
+    ED_CUDA(cudaGetLastError());
+    std::vector<double2> hres(2 * (size_t)nvec);
+    ED_CUDA(cudaMemcpyAsync(hres.data(), res, hres.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    for (int v = 0; v < nvec; ++v) {
+        out[3 * v] = hres[2 * v].x;
+        out[3 * v + 1] = hres[2 * v].y;
+        out[3 * v + 2] = hres[2 * v + 1].x;
+    }
+    return ED_OK;
+}
+
 }  // namespace ed
+
+extern "C" ed_status ed_expectation(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t nvec,
+                                    ed_stream stream, double* out) {
+    using namespace ed;
+    if (!h || !x || !out) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > 8) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    if ((dtype == ED_F64 || dtype == ED_F32) && !h->is_real)
+        return fail(ED_ERR_ARG, "complex Hamiltonian or characters need a complex dtype");
+    cudaStream_t s = (cudaStream_t)stream;
+    switch (dtype_kind(dtype)) {
+        case 0: return expectation_kind<0>(h, x, nvec, s, out);
+        case 1: return expectation_kind<1>(h, x, nvec, s, out);
+        case 2: return expectation_kind<2>(h, x, nvec, s, out);
+        default: return expectation_kind<3>(h, x, nvec, s, out);
+    }
+}
 
 extern "C" ed_status ed_tridiag_eigs(const double* alpha, const double* beta, int32_t n, int32_t k, double eps_vectors,
                                      int32_t filter, double* evals, int32_t* n_found) {

@@ -104,6 +104,7 @@ def lib():
         L.ed_apply_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp, P(c_i32)]
         L.ed_apply_set_blocks.argtypes = [c_vp, ctypes.c_int, c_i32, c_i32]
         L.ed_tridiag_eigs.argtypes = [P(c_dbl), P(c_dbl), c_i32, c_i32, c_dbl, c_i32, P(c_dbl), P(c_i32)]
+        L.ed_expectation.argtypes = [c_vp, ctypes.c_int, c_vp, c_i32, c_vp, P(c_dbl)]
         L.ed_batch_free.argtypes = [c_vp]
         L.ed_batch_free.restype = None
         L.ed_lanczos_batch.argtypes = [c_vp, P(ed_block_lanczos_opts), P(c_dbl), P(ed_block_lanczos_report), c_vp]
@@ -113,7 +114,7 @@ def lib():
         L.ed_version.restype = ctypes.c_char_p
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
-                  "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs"):
+                  "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -257,6 +258,20 @@ class Hamiltonian:
             stream = torch.cuda.current_stream(x.device)
         self.apply_ptr(dt, x.data_ptr(), y.data_ptr(), nvec, stream)
         return y
+
+    def expectation(self, x, stream=None):
+        """ed_expectation: <x|H|x> / <x|x> for a torch CUDA tensor of shape [D] or [nvec, D]
+        (complex numpy array, one entry per vector)."""
+        import torch
+        dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
+        if not x.is_cuda or not x.is_contiguous() or x.shape[-1] != self.dim:
+            raise ValueError("x must be a contiguous CUDA tensor with last dimension = basis dimension")
+        nvec = 1 if x.dim() == 1 else x.shape[0]
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        out = np.zeros((nvec, 3), np.float64)
+        check(lib().ed_expectation(self.handle, dt, x.data_ptr(), nvec, _stream_handle(stream), _ptr(out, c_dbl)))
+        return (out[:, 0] + 1j * out[:, 1]) / out[:, 2]
 
     def autotune(self, x, y, stream=None):
         """ed_apply_autotune on torch CUDA tensors shaped as for apply(); returns blocks per SM."""
