@@ -21,7 +21,8 @@ Large-Scale Exact Diagonalization" and the sections it builds on):
   * eigenvalues: dense LAPACK or ARPACK on the CSR -- `lowest_eigs`;
   * matrix-free sampled rows with keyed-random x -- `rows`;
   * spin correlations <S_i.S_j> of a symmetric-basis state, written out in the
-    product basis (Eq. structurefactor) -- `correlation_matrix`.
+    product basis (Eq. structurefactor) -- `correlation_matrix`; scalar
+    chiralities <S_i.(S_j x S_k)> likewise -- `triangle_expectation`.
 """
 from __future__ import annotations
 
@@ -292,6 +293,34 @@ def correlation_matrix(sector, psi: np.ndarray) -> np.ndarray:
                     out[idx[t]] += m * phi[k]
             C[i, j] = float(np.real(np.vdot(phi, out))) / nrm
     return C
+
+
+def triangle_expectation(sector, psi: np.ndarray, tri) -> float:
+    """<phi|S_i . (S_j x S_k)|phi> / <phi|phi> for the ordered triangle (i, j, k),
+    phi written out as in `correlation_matrix`, the scalar triple product
+    applied through the 8x8 matrix of its definition (ops.chirality_matrix).
+    N <= 20."""
+    N = sec_N(sector)
+    states = sz_states(N, sector.n_up)
+    V, kept = projector_matrix(sector, states)
+    phi = V @ np.asarray(psi, dtype=complex)
+    M = ops.chirality_matrix()
+    idx = {int(st): k for k, st in enumerate(states)}
+    bits = [N - 1 - int(x) for x in tri]
+    out = np.zeros_like(phi)
+    for k, st in enumerate(states):
+        st = int(st)
+        a = 4 * ((st >> bits[0]) & 1) + 2 * ((st >> bits[1]) & 1) + ((st >> bits[2]) & 1)
+        for ap in range(8):
+            m = M[ap, a]
+            if m == 0:
+                continue
+            t = st & ~((1 << bits[0]) | (1 << bits[1]) | (1 << bits[2]))
+            t |= ((ap >> 2) & 1) << bits[0]
+            t |= ((ap >> 1) & 1) << bits[1]
+            t |= (ap & 1) << bits[2]
+            out[idx[t]] += m * phi[k]
+    return float(np.real(np.vdot(phi, out))) / float(np.real(np.vdot(phi, phi)))
 
 
 def sec_N(sector) -> int:

@@ -8,7 +8,8 @@ commutes with G and is applied by the library's own H.x kernels
 (ed_expectation).  From the correlations, the static structure factor of
 Eq. structurefactor, S(k) = sum_j exp(i k.(r_j - r_0)) <S_j . S_0>, here
 averaged over the reference site 0 (the same for a translation-invariant
-state).
+state).  Scalar chiralities <S_i . (S_j x S_k)> of triangles follow the same
+construction with the orbit-averaged triangle operator.
 """
 from __future__ import annotations
 
@@ -65,6 +66,25 @@ def correlations(basis, sector, psi, stream=None) -> np.ndarray:
         C[orb[:, 0], orb[:, 1]] = v
         C[orb[:, 1], orb[:, 0]] = v
     return C
+
+
+def chiralities(basis, sector, psi, triangles, stream=None) -> np.ndarray:
+    """<psi| S_i . (S_j x S_k) |psi> / <psi|psi> for each ordered triangle (i, j, k):
+    the expectation of the orbit average (1/|G|) sum_g S_g(i) . (S_g(j) x S_g(k)),
+    which commutes with G (a spin flip is a rotation by pi in spin space and
+    leaves the scalar triple product unchanged)."""
+    perm = np.asarray(sector.perm, dtype=np.int64)
+    G = len(perm)
+    out = np.empty(len(triangles))
+    for n, (i, j, k) in enumerate(np.asarray(triangles, dtype=np.int64)):
+        tris = np.stack([perm[:, i], perm[:, j], perm[:, k]], axis=1).astype(np.int32)
+        terms = _Bonds(np.zeros((0, 2), np.int32), np.zeros(0), tris, np.full(G, 1.0 / G))
+        h = Hamiltonian(basis, terms)
+        try:
+            out[n] = float(np.real(h.expectation(psi, stream=stream)[0]))
+        finally:
+            h.close()
+    return out
 
 
 def structure_factor(C: np.ndarray, positions: np.ndarray, ks: np.ndarray) -> np.ndarray:

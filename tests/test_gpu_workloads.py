@@ -130,8 +130,40 @@ def test_kagome36_chiral(P):
 
 
 def test_square40_scale(P):
-    """The largest workload: N = 40, T40 x C4 x Z2 (320 elements), D ~ 4.3e8, FP32 vectors."""
+    """The largest workload: N = 40, T40 x C4 x Z2 (320 elements), D ~ 4.3e8, FP32 and FP64 vectors."""
     import torch
     p = C.square40()
     b, reps, drawn, pos = _check_basis(P, p, 400, 7)
     _check_hx(P, p, b, reps, drawn, pos, torch.float32)
+    _check_hx(P, p, b, reps, drawn, pos, torch.float64)
+
+
+def test_triangular24_batch_bench_config(P):
+    """The batching workload as bench.py runs it: all 36 (k, rho_k) sectors of the 24-site
+    triangular torus in one batch.  Batched H.x equals per-sector H.x bit for bit; the
+    batched single-vector plain recursion (CUDA graph) gives the ground energy of the
+    Gamma.A1 sector equal to the oracle's (ARPACK on its sparse matrix) to 1e-10 relative,
+    and every sector's energy to 1e-9 of sequential ed_lanczos."""
+    import torch
+    probs = C.triangular24_sectors()
+    bases = [P.Basis(q.sector) for q in probs]
+    hs = [P.Hamiltonian(bb, q.terms) for bb, q in zip(bases, probs)]
+    batch = P.Batch(hs)
+    x = torch.randn(batch.total, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    batch.apply(x, y)
+    off = batch.row_off
+    for s in (0, 7, 18, 35):
+        xs = x[int(off[s]):int(off[s + 1])].contiguous()
+        ys = torch.empty_like(xs)
+        hs[s].apply(xs, ys)
+        torch.cuda.synchronize()
+        assert torch.equal(ys, y[int(off[s]):int(off[s + 1])])
+    ev, rep = batch.lanczos(block=1, n_eig=1, tol=1e-10, max_iter=300, seed=3, use_graph=True, reorth=False)
+    assert rep.converged_sectors == len(probs)
+    e0 = oracle.lowest_eigs(oracle.csr(probs[0]), 1)[0]
+    assert abs(ev[0, 0] - e0) <= 1e-10 * abs(e0), (ev[0, 0], e0)
+    for s, h in enumerate(hs):
+        dt = P.ED_F64 if h.is_real else P.ED_C128
+        es, _ = h.lanczos(n_eig=1, tol=1e-10, max_iter=300, dtype=dt)
+        assert abs(ev[s, 0] - es[0]) <= 1e-9 * abs(es[0])

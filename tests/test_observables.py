@@ -1,14 +1,16 @@
-"""Ground-state observables: spin correlations <S_i.S_j> and the static structure
-factor (Eq. structurefactor).
+"""Ground-state observables: spin correlations <S_i.S_j>, the static structure
+factor (Eq. structurefactor) and scalar chiralities <S_i.(S_j x S_k)>.
 
 CPU (oracle and host logic): the oracle's correlation matrix is pinned to the
 two-site singlet/triplet, the four-site ring (ground state -2: nearest
 neighbours -1/2, diagonal +1/4), the energy identity E = sum_b J_b <S_i.S_j>,
 total spin zero of a singlet (sum_ij C_ij = 0) and translation invariance; the
-pair orbits partition all pairs; the structure factor obeys its sum rule.
+pair orbits partition all pairs; the structure factor obeys its sum rule; the
+oracle's triangle chirality is the eigenvalue in the chirality's eigenstates.
 
 GPU: the library's correlations (ed_expectation on orbit-averaged bond
-operators) against the oracle's, computed from the same GPU ground state.
+and triangle operators) against the oracle's, computed from the same GPU
+ground state, and the energy identity with the chirality terms.
 Tolerance 1e-10: both are FP64 sums of O(N^2 |terms|) products of unit-size
 numbers.
 """
@@ -123,3 +125,47 @@ def test_gpu_correlations_match_oracle(name):
         assert e == pytest.approx(vals[0], abs=1e-8)
     # <x|H|x> of the full Hamiltonian is the Ritz value
     assert np.real(h.expectation(psi)[0]) == pytest.approx(vals[0], abs=1e-8)
+
+
+def test_oracle_triangle_chirality_eigenstates():
+    """Three sites, one up spin: the chirality S_0.(S_1 x S_2) has eigenvalues 0 and
+    +-sqrt(3)/4 there; in each eigenstate the expectation is the eigenvalue."""
+    from edinputs.lattice import Terms
+    s = Sector(3, 1, np.array([[0, 1, 2]], np.int32), np.zeros(1, np.uint8), np.ones(1, complex), 1)
+    t = Terms(np.zeros((0, 2), np.int32), np.zeros(0), np.array([[0, 1, 2]], np.int32), np.ones(1))
+
+    class Prob:
+        sector, terms = s, t
+    Hd, states = oracle.dense_sz(Prob)
+    w, v = np.linalg.eigh(Hd)
+    assert np.allclose(sorted(w), [-np.sqrt(3) / 4, 0, np.sqrt(3) / 4])
+    # without symmetry the symmetric basis is the product basis in increasing order
+    for e, vec in zip(w, v.T):
+        assert oracle.triangle_expectation(s, vec, (0, 1, 2)) == pytest.approx(e, abs=1e-12)
+        assert oracle.triangle_expectation(s, vec, (1, 0, 2)) == pytest.approx(-e, abs=1e-12)
+
+
+@pytest.mark.gpu
+def test_gpu_chiralities_and_energy_kagome12():
+    """Chiral kagome (J_chi = 0.3): GPU triangle chiralities against the oracle's on the
+    same GPU ground state, and E = sum_b J_b <S_i.S_j> + sum_t J_chi <chi_t>."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2210_03511_gb300 import build
+    build.build()
+    import paper_2210_03511_gb300 as P
+    from paper_2210_03511_gb300.observables import chiralities, correlations
+    p = SECTORS["kagome12_E1"]()
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    ev = torch.zeros((1, b.dim), dtype=torch.complex128, device="cuda")
+    vals, rep = h.lanczos(n_eig=1, tol=1e-12, max_iter=300, evecs=ev)
+    psi = ev[0].contiguous()
+    chi_g = chiralities(b, p.sector, psi, p.terms.tris)
+    psi_h = psi.cpu().numpy()
+    chi_o = np.array([oracle.triangle_expectation(p.sector, psi_h, t) for t in p.terms.tris])
+    assert np.allclose(chi_g, chi_o, rtol=0, atol=1e-10), np.abs(chi_g - chi_o).max()
+    Cg = correlations(b, p.sector, psi)
+    e = sum(J * Cg[i, j] for (i, j), J in zip(p.terms.bonds, p.terms.J)) + float(np.dot(p.terms.Jchi, chi_g))
+    assert e == pytest.approx(vals[0], abs=1e-8)
