@@ -90,3 +90,13 @@ def test_kagome_triangles_orientation():
         v = cl.pos[k] - cl.pos[i]
         # minimal images
         assert u[0] * v[1] - u[1] * v[0] != 0
+
+
+def test_square32_all_sectors_partition_the_sz0_space():
+    """Every (k, rho_k) sector of the 32-site square cluster under translations x C4
+    (1-D irreps of each little group; C4v's 2-D irrep E appears through the C4 characters
+    +-i, i.e. complex sectors): the character-formula dimensions add up to C(32, 16)."""
+    import oracle
+    ps = C.all_sectors("square", [[4, 4], [4, -4]], 1.0, 0.5, n_sublat=4, point="rot")
+    assert sum(oracle.sector_dim_formula(p.sector) for p in ps) == oracle.binom(32, 16)
+    assert any(not p.sector.is_real for p in ps)
