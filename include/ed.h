@@ -244,8 +244,10 @@ typedef struct {
                               copies of converged eigenvalues are removed from the Ritz values (Cullum-Willoughby
                               test) and Ritz vectors come from a second pass of the recursion */
     uint64_t seed;         /* start vector v1(state) = keyed SplitMix64 uniform in [-1,1), normalised */
-    int32_t refine;        /* mixed precision (F32/C64): at most this many FP64 Lanczos steps, started from the
-                              FP32 Ritz vectors, refine the eigenvalues (0 = no refinement) */
+    int32_t refine;        /* mixed precision (F32/C64), 0 = no refinement: the FP32 phase runs until each
+                              Ritz pair's residual bound allows (or reaches the FP32 noise floor), then the
+                              Ritz vectors in FP64 get one FP64 H.x and their Rayleigh quotients; if
+                              r^2/gap misses tol, at most this many FP64 Lanczos steps from their sum */
     int32_t check_every;   /* T-matrix eigensolve every this many steps (>= 1) */
 } ed_lanczos_opts;
 
@@ -256,7 +258,8 @@ typedef struct {
     double ritz[8];            /* T-matrix eigenvalues at exit (in the vector dtype's precision) */
     double resid_bound[8];     /* beta_n |s_n,k|: Lanczos residual bound of each Ritz pair */
     double refined[8];         /* eigenvalues after the FP64 refinement (when refine) */
-    double refined_resid[8];   /* FP64 Lanczos residual bounds of the refined eigenpairs (when refine) */
+    double refined_resid[8];   /* |H y - E y| / |y| of the Rayleigh quotient, or the FP64 polish's Lanczos
+                                  residual bound (when refine) */
     double seconds;            /* wall time of the call */
 } ed_lanczos_report;
 

@@ -92,6 +92,70 @@ __global__ void multi_dot(const typename LV<K>::T* A, int64_t ld, const typename
     if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
 }
 
+// Reorthogonalisation coefficients for FP32 vectors: each thread forms
+// partial sums of 16 consecutive products in FP32 and adds them to its FP64
+// accumulator (GB300 has little FP64 throughput).  The coefficients then
+// carry a relative error ~16 eps_32 of sum |x_i y_i|, far below what
+// keeping the Lanczos vectors orthogonal to working precision needs; the
+// Lanczos coefficients alpha and beta keep full FP64 accumulation.
+template <int K>
+__global__ void multi_dot_f32(const typename LV<K>::T* A, int64_t ld, const typename LV<K>::T* b, int64_t n,
+                              double2* partial) {
+    static_assert(K == 1 || K == 3, "FP32 vectors only");
+    const typename LV<K>::T* a = A + (int64_t)blockIdx.y * ld;
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n, i0 + per);
+    double2 acc = make_double2(0, 0);
+    float cx = 0.f, cy = 0.f;
+    int cnt = 0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        if constexpr (K == 1) {
+            cx = fmaf(a[i], b[i], cx);
+        } else {
+            const float2 x = a[i], y = b[i];
+            cx = fmaf(x.x, y.x, fmaf(x.y, y.y, cx));
+            cy = fmaf(x.x, y.y, fmaf(-x.y, y.x, cy));
+        }
+        if (++cnt == 16) {
+            acc.x += (double)cx;
+            acc.y += (double)cy;
+            cx = cy = 0.f;
+            cnt = 0;
+        }
+    }
+    acc.x += (double)cx;
+    acc.y += (double)cy;
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
+}
+
+// w -= sum_k c_k A_k in FP32 arithmetic for FP32 vectors (the coefficients
+// of a reorthogonalisation are small, so the FP32 update adds no error above
+// the rounding of w itself)
+template <int K>
+__global__ void multi_axpy_f32(typename LV<K>::T* w, const typename LV<K>::T* A, int64_t ld, int nk, const double2* c,
+                               int64_t n) {
+    static_assert(K == 1 || K == 3, "FP32 vectors only");
+    __shared__ float2 cf[2048];  // nk <= max_iter + 1 <= 2001 (ed_lanczos checks max_iter)
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) cf[k] = make_float2((float)c[k].x, (float)c[k].y);
+    __syncthreads();
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (K == 1) {
+            float x = w[i];
+            for (int k = 0; k < nk; ++k) x = fmaf(-cf[k].x, A[(int64_t)k * ld + i], x);
+            w[i] = x;
+        } else {
+            float2 x = w[i];
+            for (int k = 0; k < nk; ++k) {
+                const float2 a = A[(int64_t)k * ld + i];
+                x.x -= cf[k].x * a.x - cf[k].y * a.y;
+                x.y -= cf[k].x * a.y + cf[k].y * a.x;
+            }
+            w[i] = x;
+        }
+    }
+}
+
 // out[k] = sum over nb partials (fixed order)
 __global__ void reduce_partials(const double2* partial, int nb, int nk, double2* out) {
     for (int k = blockIdx.x; k < nk; k += gridDim.x) {
@@ -447,6 +511,13 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     // unit roundoff of the vectors: copies of one eigenvalue agree to ~eps_v |T|
     const double eps_v = (K == 1 || K == 3) ? 1.1920928955078125e-07 : 2.220446049250313e-16;
     ed_dtype vdt = o->dtype;
+    // Mixed precision with refinement: the FP32 phase runs on until every
+    // wanted Ritz pair's residual bound r allows a Rayleigh quotient in FP64
+    // to meet the final tolerance (its error is at most r^2/gap), or until r
+    // reaches the FP32 noise floor ~2 eps_32 |T| (the rounding of the FP32
+    // Lanczos vectors alone leaves a residual of that size).
+    const bool rq_refine = (K == 1 || K == 3) && o->refine > 0;
+    std::vector<double> lam_full, rb_full;  // last check: n_eig + 1 Ritz values, residual bounds
     for (int n = 0; n < max_it; ++n) {
         ed_status st = apply_launch(h, vdt, vec(n), w, 1, s);
         if (st != ED_OK) return st;
@@ -456,8 +527,14 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         lanczos_axpy<K><<<g, 256, 0, s>>>(w, vec(n), n > 0 ? vec(n - 1) : nullptr, D, alpha_d, beta_d);
         if (o->reorth) {
             for (int pass = 0; pass < 2; ++pass) {
-                dot(V, n + 1, w, coef);
-                multi_axpy<K><<<g, 256, 0, s>>>(w, V, D, n + 1, coef, D);
+                if constexpr (K == 1 || K == 3) {
+                    multi_dot_f32<K><<<dim3(z.nb, n + 1), 256, 0, s>>>(V, D, w, D, partial);
+                    reduce_partials<<<std::min(n + 1, 1024), 256, 0, s>>>(partial, z.nb, n + 1, coef);
+                    multi_axpy_f32<K><<<g, 256, 0, s>>>(w, V, D, n + 1, coef, D);
+                } else {
+                    dot(V, n + 1, w, coef);
+                    multi_axpy<K><<<g, 256, 0, s>>>(w, V, D, n + 1, coef, D);
+                }
             }
         }
         dot(w, 1, w, coef + n + 1);
@@ -474,15 +551,18 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         const bool breakdown = bh < 1e-13 * tnorm;
         const bool last = breakdown || n + 1 == max_it;
         if ((n + 1) % every == 0 || last) {
+            double tn = 0.0;
+            for (int i = 0; i < iters; ++i)
+                tn = std::max(tn, fabs(al[i]) + (i > 0 ? be[i - 1] : 0.0) + (i + 1 < iters ? be[i] : 0.0));
             if (o->reorth) {
                 tri_eig(al, be, iters, n_eig + 1, lam, svec);
             } else {
-                double tn = 0.0;
-                for (int i = 0; i < iters; ++i)
-                    tn = std::max(tn, fabs(al[i]) + (i > 0 ? be[i - 1] : 0.0) + (i + 1 < iters ? be[i] : 0.0));
                 tri_eig_filtered(al, be, iters, n_eig + 1, 100.0 * eps_v * tn, 1e3 * 2.220446049250313e-16 * tn, lam,
                                  svec);
             }
+            lam_full = lam;
+            rb_full.assign(lam.size(), 0.0);
+            for (size_t p = 0; p < lam.size(); ++p) rb_full[p] = bh * fabs(svec[p][iters - 1]);
             // converged: for each wanted Ritz value, a small change since the
             // last check and a small residual bound r = beta |s_last| (the
             // eigenvalue error is at most min(r, r^2/gap)); with eigenvectors
@@ -495,7 +575,8 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
                 for (int p = 0; p < (int)lam.size(); ++p)
                     if (p != k) gap = std::min(gap, fabs(lam[p] - lam[k]));
                 const bool steady = fabs(lam[k] - prev[k]) <= 0.1 * tol * sc;
-                const bool small_res = rb <= tol * sc || rb * rb <= tol * sc * gap;
+                const bool small_res = rq_refine ? (rb * rb <= 0.25 * o->tol * sc * gap || rb <= 2.0 * eps_v * tn)
+                                                 : (rb <= tol * sc || rb * rb <= tol * sc * gap);
                 const bool vec_ok = !evecs || rb <= sqrt(tol) * sc;
                 if (!(steady && small_res && vec_ok)) ok = false;
             }
@@ -533,18 +614,23 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     std::vector<double> ssum(iters, 0.0);
     for (int k = 0; k < nk; ++k)
         for (int i = 0; i < iters; ++i) ssum[i] += svec[k][i];
+    // FP64 Ritz vectors of the refinement: slots 0..nk-1 one per wanted pair,
+    // slot nk their sum (the start of the fallback polish)
+    const int ny = want_refine ? nk + 1 : 0;
     if (want_refine) {
-        y64 = (T64*)z.get((size_t)D * sizeof(T64));
+        y64 = (T64*)z.get((size_t)ny * D * sizeof(T64));
         if (!y64) return fail(ED_ERR_NOMEM, "refinement workspace");
     }
     if (!o->reorth && nk > 0 && (evecs || want_refine)) {
         const int nacc = evecs ? nk : 0;
+        const int ncol = nacc + ny;
         std::vector<double2> alh(iters);
         for (int j = 0; j < iters; ++j) alh[j] = make_double2(al[j], 0.0);
-        std::vector<double> sc((size_t)iters * (nacc + 1));
+        std::vector<double> sc((size_t)iters * std::max(ncol, 1));
         for (int j = 0; j < iters; ++j) {
-            for (int k = 0; k < nacc; ++k) sc[(size_t)j * (nacc + 1) + k] = svec[k][j];
-            sc[(size_t)j * (nacc + 1) + nacc] = ssum[j];
+            for (int k = 0; k < nacc; ++k) sc[(size_t)j * ncol + k] = svec[k][j];
+            for (int k = 0; k < ny - 1; ++k) sc[(size_t)j * ncol + nacc + k] = svec[k][j];
+            if (ny) sc[(size_t)j * ncol + nacc + ny - 1] = ssum[j];
         }
         double2* al_d = (double2*)z.get((size_t)iters * sizeof(double2));
         double* be_d = (double*)z.get((size_t)iters * sizeof(double));
@@ -554,7 +640,7 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         ED_CUDA(cudaMemcpyAsync(be_d, be.data(), (size_t)iters * sizeof(double), cudaMemcpyHostToDevice, s));
         ED_CUDA(cudaMemcpyAsync(sc_d, sc.data(), sc.size() * sizeof(double), cudaMemcpyHostToDevice, s));
         if (evecs) ED_CUDA(cudaMemsetAsync(evecs, 0, (size_t)nk * D * sizeof(T), s));
-        if (y64) ED_CUDA(cudaMemsetAsync(y64, 0, (size_t)D * sizeof(T64), s));
+        if (y64) ED_CUDA(cudaMemsetAsync(y64, 0, (size_t)ny * D * sizeof(T64), s));
         // v_1 exactly as in the first pass
         if (start) ED_CUDA(cudaMemcpyAsync(vec(0), start, (size_t)D * sizeof(T), cudaMemcpyDeviceToDevice, s));
         else if (h->basis->word == 8)
@@ -564,9 +650,9 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
         scale_by<K><<<g, 256, 0, s>>>(vec(0), vec(0), D, beta_d);
         for (int j = 0; j < iters; ++j) {
-            const double* cj = sc_d + (size_t)j * (nacc + 1);
+            const double* cj = sc_d + (size_t)j * ncol;
             if (nacc) accumulate<K, T><<<g, 256, 0, s>>>((T*)evecs, D, nacc, cj, vec(j), D);
-            if (y64) accumulate<K, T64><<<g, 256, 0, s>>>(y64, D, 1, cj + nacc, vec(j), D);
+            if (y64) accumulate<K, T64><<<g, 256, 0, s>>>(y64, D, ny, cj + nacc, vec(j), D);
             if (j + 1 == iters) break;
             ed_status st = apply_launch(h, vdt, vec(j), w, 1, s);
             if (st != ED_OK) return st;
@@ -594,36 +680,97 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
             ED_CUDA(cudaStreamSynchronize(s));
         }
     }
-    // Mixed precision: FP64 Lanczos polish started from the sum of the FP32
-    // Ritz vectors promoted to FP64 (the Krylov space of a start vector that
-    // already overlaps the wanted eigenvectors converges in a few steps).
+    // Mixed precision refinement (Rayleigh-quotient argument, Eq. rayleighcoeff):
+    // the FP32 Ritz vectors promoted to FP64, one FP64 H.x for all of them,
+    // E_k = <y_k|H y_k> / <y_k|y_k> and r_k = |H y_k - E_k y_k| / |y_k|.  E_k is
+    // within r_k^2 / gap_k of an eigenvalue, gap_k bounded below by the other
+    // Ritz values less their residual bounds; when that meets the tolerance
+    // for every k the refinement is done, else an FP64 Lanczos polish starts
+    // from the sum of the Ritz vectors (its Krylov space already overlaps the
+    // wanted eigenvectors and converges in a few steps).
     if constexpr (K == 1 || K == 3) {
         if (want_refine) {
+            double* sd = nullptr;
             if (o->reorth) {
-                double* sd = (double*)z.get((size_t)iters * sizeof(double));
+                sd = (double*)z.get((size_t)iters * sizeof(double));
                 if (!sd) return fail(ED_ERR_NOMEM, "refinement workspace");
-                ED_CUDA(cudaMemcpyAsync(sd, ssum.data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
-                combine<K, T64><<<g, 256, 0, s>>>(y64, V, D, iters, sd, D);
+                for (int k = 0; k <= nk; ++k) {
+                    const std::vector<double>& cvec = k < nk ? svec[k] : ssum;
+                    ED_CUDA(cudaMemcpyAsync(sd, cvec.data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
+                    combine<K, T64><<<g, 256, 0, s>>>(y64 + (int64_t)k * D, V, D, iters, sd, D);
+                    ED_CUDA(cudaStreamSynchronize(s));
+                }
+            }
+            const ed_dtype d64 = K64 == 2 ? ED_C128 : ED_F64;
+            bool rq_ok = false;
+            std::vector<double> Ek(nk), rk(nk);
+            if (rq_refine && nk <= 8) {
+                T64* w64 = (T64*)z.get((size_t)nk * D * sizeof(T64));
+                double2* part64 = (double2*)z.get((size_t)z.nb * sizeof(double2));
+                double2* res64 = (double2*)z.get((size_t)3 * nk * sizeof(double2));
+                if (!w64 || !part64 || !res64) return fail(ED_ERR_NOMEM, "refinement workspace");
+                auto dot64 = [&](const T64* a, const T64* b2, double2* out) {
+                    multi_dot<K64><<<dim3(z.nb, 1), 256, 0, s>>>(a, D, b2, D, part64);
+                    reduce_partials<<<1, 256, 0, s>>>(part64, z.nb, 1, out);
+                };
+                ed_status st = apply_launch(h, d64, y64, w64, nk, s);
+                if (st != ED_OK) return st;
+                n_apply += nk;
+                std::vector<double2> hres(2 * (size_t)nk);
+                for (int k = 0; k < nk; ++k) {
+                    dot64(y64 + (int64_t)k * D, y64 + (int64_t)k * D, res64 + 2 * k);
+                    dot64(y64 + (int64_t)k * D, w64 + (int64_t)k * D, res64 + 2 * k + 1);
+                }
+                ED_CUDA(cudaMemcpyAsync(hres.data(), res64, hres.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
                 ED_CUDA(cudaStreamSynchronize(s));
+                for (int k = 0; k < nk; ++k) {
+                    Ek[k] = hres[2 * k + 1].x / hres[2 * k].x;
+                    residual<K64><<<g, 256, 0, s>>>(w64 + (int64_t)k * D, w64 + (int64_t)k * D, y64 + (int64_t)k * D,
+                                                    D, Ek[k]);
+                    dot64(w64 + (int64_t)k * D, w64 + (int64_t)k * D, res64 + 2 * nk + k);
+                }
+                std::vector<double2> rres(nk);
+                ED_CUDA(cudaMemcpyAsync(rres.data(), res64 + 2 * nk, nk * sizeof(double2), cudaMemcpyDeviceToHost, s));
+                ED_CUDA(cudaStreamSynchronize(s));
+                rq_ok = true;
+                for (int k = 0; k < nk; ++k) {
+                    rk[k] = sqrt(std::max(0.0, rres[k].x / hres[2 * k].x));
+                    double gap = 1e300;
+                    for (size_t p = 0; p < lam_full.size(); ++p)
+                        if ((int)p != k) gap = std::min(gap, fabs(lam_full[p] - Ek[k]) - rb_full[p]);
+                    const double sc = std::max(1.0, fabs(Ek[k]));
+                    if (!(gap > 0.0) || rk[k] * rk[k] > o->tol * sc * gap) rq_ok = false;
+                }
             }
-            ed_lanczos_opts o2 = *o;
-            o2.dtype = K64 == 2 ? ED_C128 : ED_F64;
-            o2.max_iter = std::max(o->refine, o->n_eig + 2);
-            o2.refine = 0;
-            o2.check_every = 1;
-            double ev2[8];
-            ed_lanczos_report r2{};
-            ed_status st2 = run<K64>(h, &o2, ev2, nullptr, &r2, s, y64);
-            if (st2 != ED_OK && st2 != ED_ERR_NOT_CONVERGED) return st2;
-            n_apply += r2.n_apply;
-            const int n2 = std::min(nk, o->n_eig);
-            for (int k = 0; k < n2; ++k) {
-                r.refined[k] = r2.ritz[k];
-                r.refined_resid[k] = r2.resid_bound[k];
-                evals[k] = r2.ritz[k];
+            // the FP64 refinement certifies the result: its outcome decides
+            // convergence (the FP32 phase may stop at max_iter or at the
+            // dimension of a small sector without meeting its own criterion)
+            if (rq_ok) {
+                for (int k = 0; k < nk; ++k) {
+                    r.refined[k] = Ek[k];
+                    r.refined_resid[k] = rk[k];
+                    evals[k] = Ek[k];
+                }
+                conv = nk >= std::min(o->n_eig, (int)D);
+            } else {
+                ed_lanczos_opts o2 = *o;
+                o2.dtype = d64;
+                o2.max_iter = std::max(o->refine, o->n_eig + 2);
+                o2.refine = 0;
+                o2.check_every = 1;
+                double ev2[8];
+                ed_lanczos_report r2{};
+                ed_status st2 = run<K64>(h, &o2, ev2, nullptr, &r2, s, y64 + (int64_t)nk * D);
+                if (st2 != ED_OK && st2 != ED_ERR_NOT_CONVERGED) return st2;
+                n_apply += r2.n_apply;
+                const int n2 = std::min(nk, o->n_eig);
+                for (int k = 0; k < n2; ++k) {
+                    r.refined[k] = r2.ritz[k];
+                    r.refined_resid[k] = r2.resid_bound[k];
+                    evals[k] = r2.ritz[k];
+                }
+                conv = r2.converged != 0;
             }
-            conv = conv && (r2.converged != 0);
-            if (!r2.converged) conv = false;
         }
     }
     (void)mixed;
