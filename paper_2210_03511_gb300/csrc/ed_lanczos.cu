@@ -755,6 +755,7 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
             } else {
                 ed_lanczos_opts o2 = *o;
                 o2.dtype = d64;
+                o2.reorth = 0;  // a few steps from a close start: the plain recursion, no stored FP64 vectors
                 o2.max_iter = std::max(o->refine, o->n_eig + 2);
                 o2.refine = 0;
                 o2.check_every = 1;
