@@ -102,29 +102,10 @@ ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s) {
 ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s) {
     const ed_basis* b = h->basis;
     if (h->n_flip > 256) return fail(ED_ERR_ARG, "more than 256 flip terms are not supported");
-    HxArgs a{};
-    a.dt = b->dt;
-    a.reps = b->reps.p;
-    a.stab = (const uint16_t*)b->stab.p;
-    const uint8_t* dir = (const uint8_t*)b->limits.p;
-    a.dir_base = (const uint32_t*)dir;
-    a.dir_q = dir + b->dir_q_off();
-    a.limits = (const uint2*)(dir + b->dir_lim_off());
-    a.L = b->prefix_bits;
-    a.S = 1 << b->ht.m;
-    a.flips = (const FlipTerm*)h->d_flips.p;
-    a.n_flip = h->n_flip;
-    a.diag_pos = (const int8_t*)h->d_diag_pos.p;
-    a.diag_cls = (const DiagClass*)h->d_diag_cls.p;
-    a.n_diag_cls = h->n_diag_cls;
-    a.n_diag_bonds = h->n_diag_bonds;
-    a.jhs = (const double*)h->d_jhs.p;
-    a.jcls = (const uint8_t*)h->d_jcls.p;
-    a.n_jc = h->n_jc;
+    HxArgs a = make_args(h);
     a.x = x;
     a.y = y;
     a.nvec = nvec;
-    a.D = b->dim;
     a.counters = (unsigned long long*)h->d_counters.p;
     ED_CUDA(cudaMemsetAsync(h->d_counters.p, 0, 24, s));
     const bool w8 = b->word == 8, ch = b->dt.chunk_lo > 0;
