@@ -343,8 +343,9 @@ typedef struct {
     uint64_t seed;         /* Gaussian start blocks from keyed SplitMix64 of (seed, column, state) */
     int32_t use_graph;     /* 1: capture one step (all kernels, all sectors) as a CUDA graph and replay it */
     int32_t check_every;   /* eigenvalue check every this many steps */
-    int32_t reorth;        /* 1: full reorthogonalisation (classical Gram-Schmidt twice against all stored
-                              blocks); 0: the plain recursion (only the last two vectors), spurious copies
+    int32_t reorth;        /* 1: full reorthogonalisation (classical Gram-Schmidt against all stored blocks
+                              and a second pass against the last two); 0: the plain recursion (only the
+                              last two vectors), spurious copies
                               of converged eigenvalues removed as in ed_lanczos; needs block = 1 (with
                               larger blocks copies could not be told from multiplicities: ED_ERR_ARG) */
 } ed_block_lanczos_opts;
@@ -360,8 +361,9 @@ typedef struct {
 
 /* ed_lanczos_batch -- block Lanczos (the block form of Eqs.
  * lanczosrecursionabbrev and tmatrix with b x b blocks) on every sector of the
- * batch at once, with full reorthogonalisation (classical Gram-Schmidt twice
- * against all stored blocks) or the plain recursion (opts.reorth) and
+ * batch at once, with full reorthogonalisation (classical Gram-Schmidt against
+ * all stored blocks, then again against the last two, where the new block's
+ * large components lie) or the plain recursion (opts.reorth) and
  * Cholesky QR twice for the new block; a sector whose values have settled
  * stops iterating (its rows are skipped by later steps); inner
  * products in FP64 with a fixed reduction order.  evals: HOST [n][n_eig]

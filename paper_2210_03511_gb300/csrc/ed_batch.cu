@@ -638,11 +638,18 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     auto step = [&]() -> ed_status {
         ed_status st = apply_batch_launch(L, s);  // W = H V_k
         if (st != ED_OK) return st;
+        // Classical Gram-Schmidt against the stored blocks, then a second pass
+        // against the last two: W = H V_k has large components only along
+        // V_k and V_{k-1} (the block three-term relation); the first pass
+        // leaves errors of order eps |H| there and far smaller ones along
+        // older blocks, so repeating only the local part restores
+        // orthogonality at half the FP64 cost of two full passes.
         for (int pass = 0; pass < 2; ++pass) {
             double2* Cp = pass == 0 ? C1 : C2;
-            bl_gram<K><<<dim3(nt, local ? 2 : kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt, local, active);
-            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp, local);
-            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, local, active);
+            const int win = (local || pass == 1) ? 1 : 0;
+            bl_gram<K><<<dim3(nt, win ? 2 : kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt, win, active);
+            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp, win);
+            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, win, active);
         }
         cholqr(W, V, bs, dk, 1);  // V_{k+1} = W R^-1, B_k accumulated in Bacc
         bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
