@@ -383,9 +383,12 @@ def main():
         for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
                                  ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
             s_vec = {pkg.ED_F64: 8, pkg.ED_F32: 4, pkg.ED_C128: 16, pkg.ED_C64: 8}[dt]
-            # stored vectors are allocated for max_iter steps up front: 300 if they fit,
-            # else 100 (the runs here converge in under 80 steps), else no storage
-            reorth, max_it = next(((True, m) for m in (300, 100) if m * D * s_vec < 180e9), (False, 300))
+            # stored vectors are allocated for max_iter steps up front: 300 if they fit;
+            # FP32 vectors (reorthogonalised in FP32 arithmetic, cheap) also 100 (the runs
+            # here converge in under 80 steps); else no storage (FP64 Gram-Schmidt on the
+            # large sectors costs more than the plain recursion saves)
+            sizes = (300, 100) if refine else (300,)
+            reorth, max_it = next(((True, m) for m in sizes if m * D * s_vec < 180e9), (False, 300))
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=max_it, dtype=dt, reorth=reorth,

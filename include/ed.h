@@ -237,10 +237,11 @@ typedef struct {
     ed_dtype dtype;        /* vector type: F64/C128 plain, F32/C64 mixed (FP64 reductions) */
     int32_t n_eig;         /* lowest eigenvalues wanted, 1..8 */
     double tol;            /* convergence tolerance on eigenvalues (relative, e.g. 1e-10); with F32/C64
-                              vectors the FP32 phase stops at max(tol, 1e-6) and tol applies to the refinement */
+                              vectors and refine > 0, tol applies to the refined values */
     int32_t max_iter;      /* Lanczos steps at most (<= 2000) */
-    int32_t reorth;        /* 1 = full reorthogonalisation (classical Gram-Schmidt twice) against stored
-                              vectors; 0 = the plain three-term recursion (three vectors in memory): spurious
+    int32_t reorth;        /* 1 = full reorthogonalisation (classical Gram-Schmidt against all stored
+                              vectors, then again against the last two; max_iter + 1 vectors are stored);
+                              0 = the plain three-term recursion (three vectors in memory): spurious
                               copies of converged eigenvalues are removed from the Ritz values (Cullum-Willoughby
                               test) and Ritz vectors come from a second pass of the recursion */
     uint64_t seed;         /* start vector v1(state) = keyed SplitMix64 uniform in [-1,1), normalised */

@@ -3,7 +3,8 @@
 //
 // Per step: w = H v_n; alpha_n = Re<v_n|w>; w -= alpha_n v_n + beta_n v_{n-1};
 // optionally full reorthogonalisation against all stored v (classical
-// Gram-Schmidt, twice); beta_{n+1} = ||w||; v_{n+1} = w / beta_{n+1}.
+// Gram-Schmidt, then once more against v_{n-1}, v_n); beta_{n+1} = ||w||;
+// v_{n+1} = w / beta_{n+1}.
 // Vectors are stored in the caller's dtype; every inner product accumulates
 // in FP64 with a fixed reduction tree (deterministic).  alpha and beta stay on
 // the device for the vector updates and are copied to the host for the
@@ -526,14 +527,20 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         // beta_d still holds beta_n from the previous step
         lanczos_axpy<K><<<g, 256, 0, s>>>(w, vec(n), n > 0 ? vec(n - 1) : nullptr, D, alpha_d, beta_d);
         if (o->reorth) {
+            // classical Gram-Schmidt against all stored vectors, then again
+            // against the last two (v_{n-1}, v_n), where the three-term step
+            // leaves the largest rounding components
             for (int pass = 0; pass < 2; ++pass) {
+                const int j0 = pass == 0 ? 0 : std::max(0, n - 1);
+                const int nj = n + 1 - j0;
+                const T* Vj = V + (int64_t)j0 * D;
                 if constexpr (K == 1 || K == 3) {
-                    multi_dot_f32<K><<<dim3(z.nb, n + 1), 256, 0, s>>>(V, D, w, D, partial);
-                    reduce_partials<<<std::min(n + 1, 1024), 256, 0, s>>>(partial, z.nb, n + 1, coef);
-                    multi_axpy_f32<K><<<g, 256, 0, s>>>(w, V, D, n + 1, coef, D);
+                    multi_dot_f32<K><<<dim3(z.nb, nj), 256, 0, s>>>(Vj, D, w, D, partial);
+                    reduce_partials<<<std::min(nj, 1024), 256, 0, s>>>(partial, z.nb, nj, coef);
+                    multi_axpy_f32<K><<<g, 256, 0, s>>>(w, Vj, D, nj, coef, D);
                 } else {
-                    dot(V, n + 1, w, coef);
-                    multi_axpy<K><<<g, 256, 0, s>>>(w, V, D, n + 1, coef, D);
+                    dot(Vj, nj, w, coef);
+                    multi_axpy<K><<<g, 256, 0, s>>>(w, Vj, D, nj, coef, D);
                 }
             }
         }
