@@ -293,6 +293,18 @@ ed_status ed_lanczos(const ed_hamiltonian* h, const ed_lanczos_opts* opts, doubl
 ed_status ed_expectation(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t nvec, ed_stream stream,
                          double* out);
 
+/* ed_time_evolve -- psi <- exp(-i H dt) psi by one Krylov step: m (2..64)
+ * Lanczos vectors from psi with full reorthogonalisation, the m x m
+ * tridiagonal T = V^H H V (Eq. tmatrix) diagonalised on the host, and
+ * psi_new = |psi| V exp(-i T dt) e_1 (the Krylov propagator behind the
+ * thesis's Lanczos time evolution).  psi: DEVICE [D] of ED_C128 or ED_C64,
+ * overwritten.  *err (if non-NULL) = |psi| beta_m |(exp(-i T dt) e_1)_m|,
+ * the standard estimate of the step's error; *m_used (if non-NULL) the
+ * Krylov dimension used (smaller when psi spans an invariant subspace).
+ * Workspace (m + 1 vectors) from the basis's allocator.  Synchronous. */
+ed_status ed_time_evolve(const ed_hamiltonian* h, ed_dtype dtype, void* psi, double dt, int32_t m, ed_stream stream,
+                         double* err, int32_t* m_used);
+
 /* Lowest k eigenvalues of a Lanczos T-matrix (Eq. tmatrix: diagonal alpha[n],
  * off-diagonal beta[n-1], HOST arrays) by Sturm bisection in FP64, the solver
  * ed_lanczos uses.  filter = 1 applies its treatment of the plain recursion:

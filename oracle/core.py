@@ -22,7 +22,8 @@ Large-Scale Exact Diagonalization" and the sections it builds on):
   * matrix-free sampled rows with keyed-random x -- `rows`;
   * spin correlations <S_i.S_j> of a symmetric-basis state, written out in the
     product basis (Eq. structurefactor) -- `correlation_matrix`; scalar
-    chiralities <S_i.(S_j x S_k)> likewise -- `triangle_expectation`.
+    chiralities <S_i.(S_j x S_k)> likewise -- `triangle_expectation`;
+  * time evolution exp(-iHt) psi on the sparse matrix (library step) -- `evolve`.
 """
 from __future__ import annotations
 
@@ -321,6 +322,13 @@ def triangle_expectation(sector, psi: np.ndarray, tri) -> float:
             t |= (ap & 1) << bits[2]
             out[idx[t]] += m * phi[k]
     return float(np.real(np.vdot(phi, out))) / float(np.real(np.vdot(phi, phi)))
+
+
+def evolve(H, psi: np.ndarray, t: float) -> np.ndarray:
+    """exp(-i H t) psi for the oracle's sparse matrix H (scipy's expm_multiply,
+    the truncated Taylor method of Al-Mohy and Higham, as a library step)."""
+    import scipy.sparse.linalg as sla
+    return sla.expm_multiply(-1j * t * sp.csr_matrix(H), np.asarray(psi, dtype=complex))
 
 
 def sec_N(sector) -> int:

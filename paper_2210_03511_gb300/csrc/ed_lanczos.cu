@@ -220,6 +220,21 @@ __global__ void combine(O* out, const typename LV<K>::T* A, int64_t ld, int nk, 
     }
 }
 
+// out = sum_k c_k A_k with complex coefficients c (FP64 accumulation)
+template <int K>
+__global__ void combine_c(typename LV<K>::T* out, const typename LV<K>::T* A, int64_t ld, int nk, const double2* c,
+                          int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 x = make_double2(0, 0);
+        for (int k = 0; k < nk; ++k) {
+            const double2 a = ld2(A[(int64_t)k * ld + i]);
+            x.x += c[k].x * a.x - c[k].y * a.y;
+            x.y += c[k].x * a.y + c[k].y * a.x;
+        }
+        st2(out[i], x);
+    }
+}
+
 // out_k += c[k] v for k < nk (out_k = out + k*ldo): the second pass of the
 // plain recursion builds Ritz vectors one Lanczos vector at a time
 template <int K, typename O>
@@ -835,7 +850,157 @@ static ed_status expectation_kind(const ed_hamiltonian* h, const void* x, int nv
     return ED_OK;
 }
 
+// All eigenpairs of a small dense real symmetric matrix (cyclic Jacobi
+// rotations, Golub & Van Loan sec. 8.5): A (n x n, row-major) is overwritten,
+// lam[k] and column k of Q (Q[i*n + k]) are the k-th eigenpair.
+static void jacobi_eig(std::vector<double>& A, int n, std::vector<double>& lam, std::vector<double>& Q) {
+    Q.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < n; ++i)
+            for (int j = 0; j < n; ++j) {
+                const double v = A[(size_t)i * n + j] * A[(size_t)i * n + j];
+                tot += v;
+                if (i != j) off += v;
+            }
+        if (off <= 1e-32 * tot || off == 0.0) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                if (apq == 0.0) continue;
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                const double theta = (aqq - app) / (2.0 * apq);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {  // A <- A J (columns p, q)
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {  // A <- J^T A (rows p, q)
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {  // Q <- Q J
+                    const double qkp = Q[(size_t)k * n + p], qkq = Q[(size_t)k * n + q];
+                    Q[(size_t)k * n + p] = c * qkp - sn * qkq;
+                    Q[(size_t)k * n + q] = sn * qkp + c * qkq;
+                }
+            }
+    }
+    lam.resize(n);
+    for (int i = 0; i < n; ++i) lam[i] = A[(size_t)i * n + i];
+}
+
+// psi <- exp(-i H dt) psi by one Krylov step: m Lanczos vectors from psi
+// (full reorthogonalisation), T = V^H H V tridiagonal, and
+// psi_new = |psi| V exp(-i T dt) e_1.  err = |psi| beta_m |[exp(-i T dt) e_1]_m|,
+// the usual a-posteriori estimate of the step's error.
+template <int K>
+static ed_status evolve_kind(const ed_hamiltonian* h, void* psi, double dt, int m, cudaStream_t s, double* err,
+                             int* m_used) {
+    using T = typename LV<K>::T;
+    Lz<K> z;
+    z.h = h;
+    z.b = h->basis;
+    z.s = s;
+    z.D = h->basis->dim;
+    ED_CUDA(cudaDeviceGetAttribute(&z.sms, cudaDevAttrMultiProcessorCount, h->basis->device));
+    const int64_t D = z.D;
+    m = (int)std::min<int64_t>(m, D);
+    z.nb = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (D + 4095) / 4096));
+    T* V = (T*)z.get((size_t)(m + 1) * D * sizeof(T));
+    T* w = (T*)z.get((size_t)D * sizeof(T));
+    double2* partial = (double2*)z.get((size_t)(m + 2) * z.nb * sizeof(double2));
+    double2* coef = (double2*)z.get((size_t)(m + 2) * sizeof(double2));
+    double* beta_d = (double*)z.get(2 * sizeof(double));
+    double2* alpha_d = (double2*)z.get(sizeof(double2));
+    if (!V || !w || !partial || !coef || !beta_d || !alpha_d) return fail(ED_ERR_NOMEM, "time-evolution workspace");
+    const unsigned g = z.grid();
+    auto dot = [&](const T* A, int nk, const T* bv, double2* out) {
+        multi_dot<K><<<dim3(z.nb, nk), 256, 0, s>>>(A, D, bv, D, partial);
+        reduce_partials<<<std::min(nk, 1024), 256, 0, s>>>(partial, z.nb, nk, out);
+    };
+    // v_0 = psi / |psi|
+    ED_CUDA(cudaMemcpyAsync(V, psi, (size_t)D * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    dot(V, 1, V, coef);
+    sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
+    double nrm = 0.0;
+    ED_CUDA(cudaMemcpyAsync(&nrm, beta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ED_CUDA(cudaStreamSynchronize(s));
+    if (!(nrm > 0.0)) return fail(ED_ERR_ARG, "psi is zero");
+    scale_by<K><<<g, 256, 0, s>>>(V, V, D, beta_d);
+    std::vector<double> al, be;
+    int mm = 0;
+    for (int n = 0; n < m; ++n) {
+        T* vn = V + (int64_t)n * D;
+        ed_status st = apply_launch(h, K == 2 ? ED_C128 : ED_C64, vn, w, 1, s);
+        if (st != ED_OK) return st;
+        dot(vn, 1, w, alpha_d);
+        lanczos_axpy<K><<<g, 256, 0, s>>>(w, vn, n > 0 ? vn - D : nullptr, D, alpha_d, beta_d);
+        for (int pass = 0; pass < 2; ++pass) {
+            const int j0 = pass == 0 ? 0 : std::max(0, n - 1);
+            const int nj = n + 1 - j0;
+            dot(V + (int64_t)j0 * D, nj, w, coef);
+            multi_axpy<K><<<g, 256, 0, s>>>(w, V + (int64_t)j0 * D, D, nj, coef, D);
+        }
+        dot(w, 1, w, coef + m + 1);
+        sqrt_re<<<1, 1, 0, s>>>(coef + m + 1, beta_d);
+        double2 ah;
+        double bh;
+        ED_CUDA(cudaMemcpyAsync(&ah, alpha_d, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaMemcpyAsync(&bh, beta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        al.push_back(ah.x);
+        be.push_back(bh);
+        mm = n + 1;
+        // an invariant subspace: the step is exact in it
+        if (bh < 1e-14 * (fabs(ah.x) + 1.0)) break;
+        scale_by<K><<<g, 256, 0, s>>>(V + (int64_t)(n + 1) * D, w, D, beta_d);
+    }
+    ED_CUDA(cudaGetLastError());
+    // exp(-i T dt) e_1 from the eigenpairs of T
+    std::vector<double> Td((size_t)mm * mm, 0.0), lam, Q;
+    for (int i = 0; i < mm; ++i) {
+        Td[(size_t)i * mm + i] = al[i];
+        if (i + 1 < mm) Td[(size_t)i * mm + i + 1] = Td[(size_t)(i + 1) * mm + i] = be[i];
+    }
+    jacobi_eig(Td, mm, lam, Q);
+    std::vector<double2> c(mm);
+    for (int j = 0; j < mm; ++j) {
+        double re = 0.0, im = 0.0;
+        for (int k = 0; k < mm; ++k) {
+            const double q = Q[(size_t)j * mm + k] * Q[(size_t)0 * mm + k];
+            re += q * cos(lam[k] * dt);
+            im -= q * sin(lam[k] * dt);
+        }
+        c[j] = make_double2(nrm * re, nrm * im);
+    }
+    if (err) *err = be[mm - 1] * sqrt(c[mm - 1].x * c[mm - 1].x + c[mm - 1].y * c[mm - 1].y);
+    if (m_used) *m_used = mm;
+    double2* c_d = (double2*)z.get((size_t)mm * sizeof(double2));
+    if (!c_d) return fail(ED_ERR_NOMEM, "time-evolution workspace");
+    ED_CUDA(cudaMemcpyAsync(c_d, c.data(), (size_t)mm * sizeof(double2), cudaMemcpyHostToDevice, s));
+    combine_c<K><<<g, 256, 0, s>>>((T*)psi, V, D, mm, c_d, D);
+    ED_CUDA(cudaGetLastError());
+    ED_CUDA(cudaStreamSynchronize(s));
+    return ED_OK;
+}
+
 }  // namespace ed
+
+extern "C" ed_status ed_time_evolve(const ed_hamiltonian* h, ed_dtype dtype, void* psi, double dt, int32_t m,
+                                    ed_stream stream, double* err, int32_t* m_used) {
+    using namespace ed;
+    if (!h || !psi) return fail(ED_ERR_ARG, "null argument");
+    if (m < 2 || m > 64) return fail(ED_ERR_ARG, "Krylov dimension out of range [2,64]");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == ED_C128) return evolve_kind<2>(h, psi, dt, m, s, err, m_used);
+    if (dtype == ED_C64) return evolve_kind<3>(h, psi, dt, m, s, err, m_used);
+    return fail(ED_ERR_ARG, "time evolution needs complex vectors (ED_C128 or ED_C64)");
+}
 
 extern "C" ed_status ed_expectation(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t nvec,
                                     ed_stream stream, double* out) {

@@ -105,6 +105,7 @@ def lib():
         L.ed_apply_set_blocks.argtypes = [c_vp, ctypes.c_int, c_i32, c_i32]
         L.ed_tridiag_eigs.argtypes = [P(c_dbl), P(c_dbl), c_i32, c_i32, c_dbl, c_i32, P(c_dbl), P(c_i32)]
         L.ed_expectation.argtypes = [c_vp, ctypes.c_int, c_vp, c_i32, c_vp, P(c_dbl)]
+        L.ed_time_evolve.argtypes = [c_vp, ctypes.c_int, c_vp, c_dbl, c_i32, c_vp, P(c_dbl), P(c_i32)]
         L.ed_batch_free.argtypes = [c_vp]
         L.ed_batch_free.restype = None
         L.ed_lanczos_batch.argtypes = [c_vp, P(ed_block_lanczos_opts), P(c_dbl), P(ed_block_lanczos_report), c_vp]
@@ -114,7 +115,8 @@ def lib():
         L.ed_version.restype = ctypes.c_char_p
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
-                  "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation"):
+                  "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation",
+                  "ed_time_evolve"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -259,6 +261,21 @@ class Hamiltonian:
         self.apply_ptr(dt, x.data_ptr(), y.data_ptr(), nvec, stream)
         return y
 
+    def evolve(self, psi, dt, m=30, stream=None):
+        """ed_time_evolve: psi <- exp(-i H dt) psi in place (complex torch CUDA tensor [D]);
+        returns (error estimate, Krylov dimension used)."""
+        import torch
+        dt_ = {torch.complex64: ED_C64, torch.complex128: ED_C128}[psi.dtype]
+        if not psi.is_cuda or not psi.is_contiguous() or psi.numel() != self.dim:
+            raise ValueError("psi must be a contiguous CUDA tensor of the basis dimension")
+        if stream is None:
+            stream = torch.cuda.current_stream(psi.device)
+        err = c_dbl()
+        mu = c_i32()
+        check(lib().ed_time_evolve(self.handle, dt_, psi.data_ptr(), float(dt), int(m), _stream_handle(stream),
+                                   ctypes.byref(err), ctypes.byref(mu)))
+        return float(err.value), int(mu.value)
+
     def expectation(self, x, stream=None):
         """ed_expectation: <x|H|x> / <x|x> for a torch CUDA tensor of shape [D] or [nvec, D]
         (complex numpy array, one entry per vector)."""
@@ -303,7 +320,13 @@ class Hamiltonian:
         o = ed_lanczos_opts(dtype, n_eig, tol, max_iter, int(reorth), seed, refine, check_every)
         ev = (c_dbl * 8)()
         rep = ed_lanczos_report()
-        ptr = evecs.data_ptr() if evecs is not None else None
+        ptr = None
+        if evecs is not None:
+            import torch
+            want = {ED_F64: torch.float64, ED_F32: torch.float32, ED_C128: torch.complex128, ED_C64: torch.complex64}[dtype]
+            if evecs.dtype != want or not evecs.is_contiguous() or evecs.numel() < n_eig * self.dim:
+                raise ValueError(f"evecs must be a contiguous {want} tensor of n_eig x dim elements")
+            ptr = evecs.data_ptr()
         st = lib().ed_lanczos(self.handle, ctypes.byref(o), ev, ptr, ctypes.byref(rep), _stream_handle(stream))
         if st != 0 and not (st == 11 and not raise_on_nonconv):
             check(st)
