@@ -657,8 +657,13 @@ def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: i
     new_of_old[order] = np.arange(N)
     perm_new = new_of_old[perm[:, order]].astype(np.int32)
     sector = Sector(N, n_up, perm_new, flip, chi, len(blocks), label=f"{name}")
+    # elements that are pure translations (no point operation, no spin flip)
+    tset = {tuple(r) for r in space_group(cl, point="none", translations=True).perm.tolist()}
+    translations = [g for g in range(len(perm)) if not flip[g] and tuple(perm[g].tolist()) in tset]
+    tri_all = np.array(cl.triangles(), dtype=np.int64).reshape(-1, 3)
     meta = dict(k=k.tolist(), irrep=irrep, spinflip=spinflip, n_cells=cl.n_cells,
-                n_basis=cl.lat.n_basis, point_ops=[o[0] for o in lops], positions=cl.pos[order].tolist())
+                n_basis=cl.lat.n_basis, point_ops=[o[0] for o in lops], positions=cl.pos[order].tolist(),
+                translations=translations, triangles=new_of_old[tri_all].astype(np.int32).tolist())
     return Problem(name, sector, terms.relabel(new_of_old), meta)
 
 

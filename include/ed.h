@@ -179,6 +179,31 @@ ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, in
 ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep,
                                      int32_t* g, int32_t* nstab, uint8_t* compat, ed_stream stream);
 
+/* ed_restrict -- write vectors of one sector in the basis of a subgroup's sector.
+ *
+ * `from` is a sector of group G with 1-D irrep chi; `to` a sector of a
+ * subgroup H of G (every (perm, spin flip) of `to` is an element of `from`)
+ * whose characters are chi restricted to H, with the same n_sites and n_up
+ * (e.g. the translations of a space group, or the trivial group {e}, whose
+ * basis is the plain fixed-Sz basis).  A state of G's sector lies in H's
+ * sector: by Eq. symmetryadaptedwavefunctiontrafocharacter it transforms with
+ * chi under every element of H.  Its coefficients in the normalised
+ * projections of Eq. symmetryadaptedwavefunction1d are, for each
+ * representative sigma_i of `to` with G-representative r = g.sigma_i at
+ * index j of `from`,
+ *   y_i = chi(g) sqrt(|Stab_G(r)| |H| / (|G| |Stab_H(sigma_i)|)) x_j,
+ * and 0 when r's projector vanishes in G's sector.  Norms are preserved.
+ *   x: DEVICE [nvec][D_from], y: DEVICE [nvec][D_to], `dtype`, caller-owned,
+ *   column-major as for ed_apply, 1 <= nvec <= 8; y is overwritten.
+ * Errors: ED_ERR_ARG for null pointers, different n_sites/n_up, an element of
+ * `to` that is not in `from`, characters that differ from the restriction
+ * (by more than 1e-9), or a real dtype with complex characters of `from`;
+ * ED_ERR_INDEX_NOT_FOUND if a compatible representative is missing from
+ * `from` (internal error).  Runs on `stream` and synchronises it (one 8-byte
+ * device counter from `to`'s allocator). */
+ed_status ed_restrict(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int32_t nvec,
+                      ed_stream stream);
+
 void ed_basis_free(ed_basis* basis);
 
 /* ed_hamiltonian_create -- bind terms to a basis.

@@ -6,6 +6,7 @@ import this package.  It shares no code with the CUDA library
 `edinputs`.  Every function is pinned by tests/test_oracle_*.py against
 closed forms, the thesis's worked examples, invariants and brute force.
 """
-from .core import (apply, basis, binom, build, correlation_matrix, csr, dense_sz, evolve, lowest_eigs,  # noqa: F401
-                   num_threads, projector_matrix, rep, rows, sector_dim_formula, sz_states, triangle_expectation)
+from .core import (apply, basis, binom, build, chirality_sum, correlation_matrix, csr, dense_sz, evolve,  # noqa: F401
+                   lowest_eigs, nematic, num_threads, plain_state, product_expectation, projector_matrix, rep,
+                   restrict, rows, sector_dim_formula, sz_states, triangle_expectation)
 from .ops import bond_matrix, chirality_matrix  # noqa: F401

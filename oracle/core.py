@@ -23,7 +23,12 @@ Large-Scale Exact Diagonalization" and the sections it builds on):
   * spin correlations <S_i.S_j> of a symmetric-basis state, written out in the
     product basis (Eq. structurefactor) -- `correlation_matrix`; scalar
     chiralities <S_i.(S_j x S_k)> likewise -- `triangle_expectation`;
-  * time evolution exp(-iHt) psi on the sparse matrix (library step) -- `evolve`.
+  * time evolution exp(-iHt) psi on the sparse matrix (library step) -- `evolve`;
+  * a state written out in the product basis -- `plain_state`; its
+    coefficients in a subgroup's sector -- `restrict`; products of two bond or
+    triangle operators -- `product_expectation`; the nematic and chirality
+    order parameters (Eqs. nematicorderparameter, chiralityorderparameter)
+    term by term -- `nematic`, `chirality_sum`.
 """
 from __future__ import annotations
 
@@ -322,6 +327,95 @@ def triangle_expectation(sector, psi: np.ndarray, tri) -> float:
             t |= (ap & 1) << bits[2]
             out[idx[t]] += m * phi[k]
     return float(np.real(np.vdot(phi, out))) / float(np.real(np.vdot(phi, phi)))
+
+
+def plain_state(sector, psi: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(phi, states): the symmetric-basis state psi written out in the fixed-Sz
+    product basis, phi = sum_c psi_c v_c with the explicit projections v_c of
+    `projector_matrix` (Eq. symmetryadaptedwavefunction1d).  N <= 20."""
+    states = sz_states(sec_N(sector), sector.n_up)
+    V, _ = projector_matrix(sector, states)
+    assert V.shape[1] == len(psi)
+    return V @ np.asarray(psi, dtype=complex), states
+
+
+def restrict(sector, psi: np.ndarray, sub_sector) -> np.ndarray:
+    """Coefficients of the state of `psi` on the normalised projections of a
+    subgroup's sector: V_H^dagger (V_G psi), both written out by
+    `projector_matrix`.  N <= 20."""
+    phi, states = plain_state(sector, psi)
+    Vh, _ = projector_matrix(sub_sector, states)
+    return Vh.conj().T @ phi
+
+
+def _apply_local(N: int, states: np.ndarray, idx: dict, phi: np.ndarray, sites, M: np.ndarray) -> np.ndarray:
+    """O phi for the operator with matrix M on `sites` (row/column index: the
+    sites' bits, first site most significant) and the identity elsewhere."""
+    bits = [N - 1 - int(x) for x in sites]
+    k = len(bits)
+    mask = 0
+    for b in bits:
+        mask |= 1 << b
+    out = np.zeros_like(phi)
+    for c, st in enumerate(states):
+        st = int(st)
+        a = 0
+        for b in bits:
+            a = (a << 1) | ((st >> b) & 1)
+        for ap in range(1 << k):
+            m = M[ap, a]
+            if m == 0:
+                continue
+            t = st & ~mask
+            for l, b in enumerate(bits):
+                t |= ((ap >> (k - 1 - l)) & 1) << b
+            out[idx[t]] += m * phi[c]
+    return out
+
+
+def product_expectation(sector, psi: np.ndarray, first, second) -> complex:
+    """<phi| O_1 O_2 |phi> / <phi|phi> for two local operators, each given as
+    ("bond", (i, j)) for S_i . S_j (ops.bond_matrix) or ("tri", (i, j, k)) for
+    S_i . (S_j x S_k) (ops.chirality_matrix), phi written out as in
+    `plain_state`.  Computed as <O_1 phi | O_2 phi> (O_1 is Hermitian)."""
+    phi, states = plain_state(sector, psi)
+    N = sec_N(sector)
+    idx = {int(st): k for k, st in enumerate(states)}
+    mats = {"bond": ops.bond_matrix(), "tri": ops.chirality_matrix()}
+    u = _apply_local(N, states, idx, phi, first[1], mats[first[0]])
+    v = _apply_local(N, states, idx, phi, second[1], mats[second[0]])
+    return complex(np.vdot(u, v) / np.vdot(phi, phi))
+
+
+def nematic(sector, psi: np.ndarray, bond, bonds) -> complex:
+    """Eq. nematicorderparameter: sum over the bonds (i, j) of `bonds` (the
+    bonds parallel to `bond`) of <(S_a.S_b)(S_i.S_j)> - <S_a.S_b><S_i.S_j>,
+    each term computed directly on the written-out state.  Complex: the
+    imaginary part of a sum over a whole translation class vanishes."""
+    phi, states = plain_state(sector, psi)
+    N = sec_N(sector)
+    idx = {int(st): k for k, st in enumerate(states)}
+    M = ops.bond_matrix()
+    nrm = np.vdot(phi, phi)
+    u = _apply_local(N, states, idx, phi, bond, M)
+    ea = np.vdot(phi, u) / nrm
+    total = 0j
+    for b in bonds:
+        v = _apply_local(N, states, idx, phi, b, M)
+        total += np.vdot(u, v) / nrm - ea * (np.vdot(phi, v) / nrm)
+    return complex(total)
+
+
+def chirality_sum(sector, psi: np.ndarray, tri, tris) -> complex:
+    """Eq. chiralityorderparameter: sum over the triangles t of `tris` of
+    <chi_tri chi_t>, chi_(i,j,k) = S_i . (S_j x S_k), computed directly."""
+    phi, states = plain_state(sector, psi)
+    N = sec_N(sector)
+    idx = {int(st): k for k, st in enumerate(states)}
+    M = ops.chirality_matrix()
+    nrm = np.vdot(phi, phi)
+    u = _apply_local(N, states, idx, phi, tri, M)
+    return complex(sum(np.vdot(u, _apply_local(N, states, idx, phi, t, M)) for t in tris) / nrm)
 
 
 def evolve(H, psi: np.ndarray, t: float) -> np.ndarray:

@@ -268,6 +268,176 @@ ed_status representatives_device(const ed_basis* b, const uint64_t* st, int64_t 
     return ch ? launch_rep<uint32_t, true>(b, st, n, r, g, ns, cp, s) : launch_rep<uint32_t, false>(b, st, n, r, g, ns, cp, s);
 }
 
+// ---------------------------------------------------------------- restriction to a subgroup's sector
+// A state of G's sector transforms with chi under every h of a subgroup H
+// (Eq. symmetryadaptedwavefunctiontrafocharacter), so it lies in H's sector.
+// Its coefficient on H's normalised projection of sigma (Eq.
+// symmetryadaptedwavefunction1d) is sqrt(|H| / |Stab_H(sigma)|) <sigma|psi>, and
+// the product-state amplitude is <sigma|psi> = chi(g) sqrt(|Stab_G(r)| / |G|) x_j
+// for r = g.sigma the G-representative at index j.  One thread per row of H's
+// basis: G's representative search (tables of G), G's index search, one scaled
+// copy per vector.
+template <int K> struct RVal;
+template <> struct RVal<0> { using T = double; };
+template <> struct RVal<1> { using T = float; };
+template <> struct RVal<2> { using T = double2; };
+template <> struct RVal<3> { using T = float2; };
+
+__device__ __forceinline__ double scale_val(double2 c, double x) { return c.x * x; }
+__device__ __forceinline__ float scale_val(double2 c, float x) { return (float)(c.x * (double)x); }
+__device__ __forceinline__ double2 scale_val(double2 c, double2 x) {
+    return make_double2(c.x * x.x - c.y * x.y, c.x * x.y + c.y * x.x);
+}
+__device__ __forceinline__ float2 scale_val(double2 c, float2 x) {
+    return make_float2((float)(c.x * (double)x.x - c.y * (double)x.y), (float)(c.x * (double)x.y + c.y * (double)x.x));
+}
+template <typename T> __device__ __forceinline__ T zero_val();
+template <> __device__ __forceinline__ double zero_val<double>() { return 0.0; }
+template <> __device__ __forceinline__ float zero_val<float>() { return 0.f; }
+template <> __device__ __forceinline__ double2 zero_val<double2>() { return make_double2(0.0, 0.0); }
+template <> __device__ __forceinline__ float2 zero_val<float2>() { return make_float2(0.f, 0.f); }
+
+struct RestrictArgs {
+    DevTables dt;               // tables of G
+    const void* reps_g;         // G's basis
+    const uint32_t* dir_base;   // G's Limits directory
+    const uint8_t* dir_q;
+    const uint2* limits;
+    int L;
+    int64_t Dg;
+    const void* reps_h;         // H's basis and stabiliser orders
+    const uint16_t* stab_h;
+    int64_t Dh;
+    double ratio;               // |H| / |G|
+    const void* x;
+    void* y;
+    int nvec;
+    unsigned long long* missing;
+};
+
+template <typename W, bool CH, int K>
+__global__ void __launch_bounds__(256) restrict_kernel(RestrictArgs a) {
+    using T = typename RVal<K>::T;
+    extern __shared__ __align__(16) uint8_t smem[];
+    const TabView<CH> t = stage_whole_or_global<CH>(a.dt, smem);
+    const W* reps_g = (const W*)a.reps_g;
+    const W* reps_h = (const W*)a.reps_h;
+    const T* x = (const T*)a.x;
+    T* y = (T*)a.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.Dh; i += (int64_t)gridDim.x * blockDim.x) {
+        W r;
+        int g, ns;
+        bool cp;
+        find_rep<W, CH>(ld_ro(reps_h + i), t, r, g, ns, cp);
+        int64_t j = -1;
+        double2 c = make_double2(0.0, 0.0);
+        if (cp) {
+            j = find_index<W>(r, reps_g, a.dir_base, a.dir_q, a.limits, a.L);
+            if (j < 0) {
+                atomicAdd(a.missing, 1ull);
+            } else {
+                const double f = sqrt(a.ratio * (double)ns / (double)ld_ro(a.stab_h + i));
+                const double2 ch = t.chi[g];
+                c = make_double2(ch.x * f, ch.y * f);
+            }
+        }
+        for (int v = 0; v < a.nvec; ++v)
+            y[(int64_t)v * a.Dh + i] = j >= 0 ? scale_val(c, ld_ro(x + (int64_t)v * a.Dg + j)) : zero_val<T>();
+    }
+}
+
+template <typename W, bool CH, int K>
+static ed_status launch_restrict(const RestrictArgs& a, cudaStream_t s) {
+    auto k = restrict_kernel<W, CH, K>;
+    const size_t smem = whole_stage_bytes(a.dt);
+    ED_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int dev = 0, sms = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.Dh + 255) / 256, (int64_t)sms * 8));
+    k<<<grid, 256, smem, s>>>(a);
+    ED_CUDA(cudaGetLastError());
+    return ED_OK;
+}
+
+template <typename W, bool CH>
+static ed_status restrict_dtype(const RestrictArgs& a, ed_dtype dtype, cudaStream_t s) {
+    switch (dtype) {
+        case ED_F64: return launch_restrict<W, CH, 0>(a, s);
+        case ED_F32: return launch_restrict<W, CH, 1>(a, s);
+        case ED_C128: return launch_restrict<W, CH, 2>(a, s);
+        case ED_C64: return launch_restrict<W, CH, 3>(a, s);
+    }
+    return fail(ED_ERR_ARG, "bad dtype");
+}
+
+// Index in `g` of every element of `h` (same permutation and flip), or an
+// error if one is missing or its character differs.
+static ed_status subgroup_check(const HostTables& g, const HostTables& h) {
+    if (g.N != h.N || g.n_up != h.n_up) return fail(ED_ERR_ARG, "sectors differ in n_sites or n_up");
+    const int N = g.N;
+    for (int e = 0; e < h.G; ++e) {
+        const int32_t* pe = h.perm.data() + (size_t)e * N;
+        int found = -1;
+        for (int f = 0; f < g.G && found < 0; ++f) {
+            if (g.flip[f] != h.flip[e]) continue;
+            if (std::equal(pe, pe + N, g.perm.data() + (size_t)f * N)) found = f;
+        }
+        if (found < 0) return fail(ED_ERR_ARG, "element %d of the target group is not in the source group", e);
+        const double dr = g.chi[2 * found] - h.chi[2 * e], di = g.chi[2 * found + 1] - h.chi[2 * e + 1];
+        if (dr * dr + di * di > 1e-18)
+            return fail(ED_ERR_ARG, "character of element %d differs from the restriction of the source irrep", e);
+    }
+    return ED_OK;
+}
+
+ed_status restrict_vectors(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int nvec,
+                           cudaStream_t s) {
+    if (!from || !to || !x || !y) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > 8) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    if (dtype != ED_F64 && dtype != ED_F32 && dtype != ED_C128 && dtype != ED_C64) return fail(ED_ERR_ARG, "bad dtype");
+    ed_status st = subgroup_check(from->ht, to->ht);
+    if (st != ED_OK) return st;
+    if ((dtype == ED_F64 || dtype == ED_F32) && !from->ht.real_chars)
+        return fail(ED_ERR_ARG, "complex characters need a complex dtype");
+    if (to->dim == 0) return ED_OK;
+    RestrictArgs a{};
+    a.dt = from->dt;
+    a.reps_g = from->reps.p;
+    const uint8_t* dir = (const uint8_t*)from->limits.p;
+    a.dir_base = (const uint32_t*)dir;
+    a.dir_q = dir + from->dir_q_off();
+    a.limits = (const uint2*)(dir + from->dir_lim_off());
+    a.L = from->prefix_bits;
+    a.Dg = from->dim;
+    a.reps_h = to->reps.p;
+    a.stab_h = (const uint16_t*)to->stab.p;
+    a.Dh = to->dim;
+    a.ratio = (double)to->ht.G / (double)from->ht.G;
+    a.x = x;
+    a.y = y;
+    a.nvec = nvec;
+    a.missing = (unsigned long long*)to->alloc.get(sizeof(unsigned long long), s);
+    if (!a.missing) return fail(ED_ERR_NOMEM, "restriction counter");
+    unsigned long long missing = 0;
+    cudaError_t e = cudaMemsetAsync(a.missing, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync");
+    if (st == ED_OK) {
+        const bool w8 = from->word == 8, ch = from->dt.chunk_lo > 0;
+        st = w8 ? (ch ? restrict_dtype<uint64_t, true>(a, dtype, s) : restrict_dtype<uint64_t, false>(a, dtype, s))
+                : (ch ? restrict_dtype<uint32_t, true>(a, dtype, s) : restrict_dtype<uint32_t, false>(a, dtype, s));
+    }
+    if (st == ED_OK) {
+        e = cudaMemcpyAsync(&missing, a.missing, sizeof(missing), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "restriction");
+    }
+    to->alloc.put(a.missing, sizeof(unsigned long long), s);
+    if (st == ED_OK && missing)
+        st = fail(ED_ERR_INDEX_NOT_FOUND, "%llu compatible representatives missing from the source basis", missing);
+    return st;
+}
+
 // ---------------------------------------------------------------- no-allocation variant
 // Some callers cannot allocate device memory themselves: applications whose
 // device memory is owned by another runtime's pool (a framework that reserves

@@ -397,6 +397,12 @@ static ed_status prepare_terms(const ed_basis* b, const ed_terms* tm, ed_hamilto
 using namespace ed;
 
 // ------------------------------------------------------------------ C ABI
+namespace ed {
+// ed_basis.cu: restriction of sector vectors to a subgroup's sector.
+ed_status restrict_vectors(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int nvec,
+                           cudaStream_t s);
+}  // namespace ed
+
 extern "C" {
 
 const char* ed_last_error(void) { return g_err.c_str(); }
@@ -497,6 +503,11 @@ ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, in
 ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep,
                                      int32_t* g, int32_t* nstab, uint8_t* compat, ed_stream stream) {
     return representatives_static(sector, states, n, rep, g, nstab, compat, (cudaStream_t)stream);
+}
+
+ed_status ed_restrict(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int32_t nvec,
+                      ed_stream stream) {
+    return restrict_vectors(from, to, dtype, x, y, nvec, (cudaStream_t)stream);
 }
 
 void ed_basis_free(ed_basis* b) {

@@ -106,6 +106,7 @@ def lib():
         L.ed_tridiag_eigs.argtypes = [P(c_dbl), P(c_dbl), c_i32, c_i32, c_dbl, c_i32, P(c_dbl), P(c_i32)]
         L.ed_expectation.argtypes = [c_vp, ctypes.c_int, c_vp, c_i32, c_vp, P(c_dbl)]
         L.ed_time_evolve.argtypes = [c_vp, ctypes.c_int, c_vp, c_dbl, c_i32, c_vp, P(c_dbl), P(c_i32)]
+        L.ed_restrict.argtypes = [c_vp, c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
         L.ed_batch_free.argtypes = [c_vp]
         L.ed_batch_free.restype = None
         L.ed_lanczos_batch.argtypes = [c_vp, P(ed_block_lanczos_opts), P(c_dbl), P(ed_block_lanczos_report), c_vp]
@@ -116,7 +117,7 @@ def lib():
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
                   "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation",
-                  "ed_time_evolve"):
+                  "ed_time_evolve", "ed_restrict"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -211,6 +212,26 @@ class Basis:
         check(lib().ed_basis_export(self.handle, _ptr(reps, c_u64), _ptr(stab, c_u16)))
         return reps, stab
 
+    def restrict_to(self, sub: "Basis", x, y=None, stream=None):
+        """ed_restrict: the vectors x (torch CUDA tensor [D] or [nvec, D] in this
+        basis) written in the basis `sub` of a subgroup's sector whose characters
+        are this sector's restricted to the subgroup.  Returns y (allocated when
+        not given: same dtype, last dimension sub.dim)."""
+        import torch
+        dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
+        if not x.is_cuda or not x.is_contiguous() or x.shape[-1] != self.dim:
+            raise ValueError("x must be a contiguous CUDA tensor with last dimension = basis dimension")
+        shape = tuple(x.shape[:-1]) + (sub.dim,)
+        if y is None:
+            y = torch.empty(shape, dtype=x.dtype, device=x.device)
+        elif y.dtype != x.dtype or tuple(y.shape) != shape or not y.is_cuda or not y.is_contiguous():
+            raise ValueError("y must be a contiguous CUDA tensor of x's dtype with last dimension = sub.dim")
+        nvec = 1 if x.dim() == 1 else x.shape[0]
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        check(lib().ed_restrict(self.handle, sub.handle, dt, x.data_ptr(), y.data_ptr(), nvec, _stream_handle(stream)))
+        return y
+
     def close(self):
         if self.handle:
             lib().ed_basis_free(self.handle)
@@ -276,9 +297,10 @@ class Hamiltonian:
                                    ctypes.byref(err), ctypes.byref(mu)))
         return float(err.value), int(mu.value)
 
-    def expectation(self, x, stream=None):
+    def expectation(self, x, stream=None, raw=False):
         """ed_expectation: <x|H|x> / <x|x> for a torch CUDA tensor of shape [D] or [nvec, D]
-        (complex numpy array, one entry per vector)."""
+        (complex numpy array, one entry per vector); raw=True returns the pair
+        (<x|H|x>, <x|x>) of arrays instead."""
         import torch
         dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
         if not x.is_cuda or not x.is_contiguous() or x.shape[-1] != self.dim:
@@ -288,6 +310,8 @@ class Hamiltonian:
             stream = torch.cuda.current_stream(x.device)
         out = np.zeros((nvec, 3), np.float64)
         check(lib().ed_expectation(self.handle, dt, x.data_ptr(), nvec, _stream_handle(stream), _ptr(out, c_dbl)))
+        if raw:
+            return out[:, 0] + 1j * out[:, 1], out[:, 2].copy()
         return (out[:, 0] + 1j * out[:, 1]) / out[:, 2]
 
     def autotune(self, x, y, stream=None):

@@ -10,6 +10,17 @@ Eq. structurefactor, S(k) = sum_j exp(i k.(r_j - r_0)) <S_j . S_0>, here
 averaged over the reference site 0 (the same for a translation-invariant
 state).  Scalar chiralities <S_i . (S_j x S_k)> of triangles follow the same
 construction with the orbit-averaged triangle operator.
+
+Four- and six-spin order parameters (the nematic N of Eq.
+nematicorderparameter and the chirality correlation X of Eq.
+chiralityorderparameter) sum a product over the translates of a bond or a
+triangle.  With B = sum_{t in T} t O t^-1 the translation sum of O, a state of
+momentum k has <O B> = <B^2> / |T| (<psi|t A t^-1|psi> = <A> for every
+translation t), and <B^2> = ||B psi||^2 because B is Hermitian.  B commutes
+with the translations but not with the point group, so psi is first written in
+the basis of its translation-only sector (ed_restrict, the characters of the
+translations are those of psi's irrep) and B is applied there by the H.x
+kernels.
 """
 from __future__ import annotations
 
@@ -17,7 +28,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .ed import Hamiltonian
+from .ed import Basis, Hamiltonian
 
 
 @dataclass
@@ -98,3 +109,92 @@ def structure_factor(C: np.ndarray, positions: np.ndarray, ks: np.ndarray) -> np
         ph = np.exp(1j * (r @ k))
         out[n] = float(np.real(np.conj(ph) @ C @ ph)) / N
     return out
+
+
+@dataclass
+class SubSector:
+    """Sector of a subgroup (the fields of ed_sector)."""
+    n_sites: int
+    n_up: int
+    perm: np.ndarray
+    spinflip: np.ndarray
+    chi: np.ndarray
+    n_sublat: int
+
+
+def subgroup_sector(sector, elements) -> SubSector:
+    """The sector of the subgroup formed by `elements` (indices into the
+    sector's group, which must contain the identity, element 0) with the
+    characters of the sector's irrep restricted to it.  The sublattice blocks
+    are kept: a partition stable under a group is stable under its subgroups."""
+    idx = [int(e) for e in elements]
+    if 0 not in idx:
+        raise ValueError("the subgroup must contain the identity (element 0)")
+    idx = [0] + [e for e in idx if e != 0]
+    return SubSector(int(sector.n_sites), int(sector.n_up), np.asarray(sector.perm)[idx].astype(np.int32),
+                     np.asarray(sector.spinflip)[idx].astype(np.uint8), np.asarray(sector.chi)[idx].astype(complex),
+                     int(sector.n_sublat))
+
+
+class TranslationSector:
+    """The translation-only sector of a state's sector, its basis, and the
+    restriction of states to it (ed_restrict)."""
+
+    def __init__(self, basis, sector, translations):
+        self.basis = basis
+        self.translations = [int(t) for t in translations]
+        self.sector = subgroup_sector(sector, self.translations)
+        self.sub = Basis(self.sector)
+        self.perm = np.asarray(sector.perm, dtype=np.int64)[self.translations]
+
+    @property
+    def n_trans(self) -> int:
+        return len(self.translations)
+
+    def orbit_bonds(self, bond) -> np.ndarray:
+        a, b = int(bond[0]), int(bond[1])
+        return np.stack([self.perm[:, a], self.perm[:, b]], axis=1).astype(np.int32)
+
+    def orbit_triangles(self, tri) -> np.ndarray:
+        return np.stack([self.perm[:, int(v)] for v in tri], axis=1).astype(np.int32)
+
+    def moments(self, psi, terms, stream=None):
+        """(<B>, <B^2>) of the translation-invariant operator B given by `terms`
+        in the state psi (torch CUDA tensor in the symmetric basis of `basis`)."""
+        import torch
+        h = Hamiltonian(self.sub, terms)
+        try:
+            x = psi
+            if not h.is_real and not x.is_complex():
+                x = x.to(torch.complex128)
+            xs = self.basis.restrict_to(self.sub, x.contiguous(), stream=stream)
+            phi = torch.empty_like(xs)
+            h.apply(xs, phi, stream=stream)
+            hx, nx = h.expectation(xs, stream=stream, raw=True)
+            _, nphi = h.expectation(phi, stream=stream, raw=True)
+        finally:
+            h.close()
+        return float(np.real(hx[0]) / nx[0]), float(nphi[0] / nx[0])
+
+    def close(self):
+        self.sub.close()
+
+
+def nematic(ts: TranslationSector, psi, bond, stream=None) -> float:
+    """N of Eq. nematicorderparameter for the bond (a, b): the sum over its
+    translates (i, j) of the connected <(S_a.S_b)(S_i.S_j)> - <S_a.S_b><S_i.S_j>,
+    = (<B^2> - <B>^2) / |T| with B = sum_t S_t(a).S_t(b)."""
+    bonds = ts.orbit_bonds(bond)
+    terms = _Bonds(bonds, np.ones(len(bonds)), np.zeros((0, 3), np.int32), np.zeros(0))
+    b1, b2 = ts.moments(psi, terms, stream=stream)
+    return (b2 - b1 * b1) / ts.n_trans
+
+
+def chirality_correlation(ts: TranslationSector, psi, tri, stream=None) -> float:
+    """X of Eq. chiralityorderparameter for the triangle (i, j, k): the sum over
+    its translates t of <chi_(i,j,k) chi_t>, = <X^2> / |T| with X the
+    translation sum of chi_(i,j,k) = S_i.(S_j x S_k)."""
+    tris = ts.orbit_triangles(tri)
+    terms = _Bonds(np.zeros((0, 2), np.int32), np.zeros(0), tris, np.ones(len(tris)))
+    _, x2 = ts.moments(psi, terms, stream=stream)
+    return x2 / ts.n_trans
