@@ -204,6 +204,28 @@ ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* st
 ed_status ed_restrict(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int32_t nvec,
                       ed_stream stream);
 
+/* ed_apply_sz -- y = O x for the one-site sum O = sum_i c_i S^z_i (e.g. the
+ * Fourier component S^z(q) = N^-1/2 sum_i exp(i q.r_i) S^z_i probed by the
+ * dynamical spin structure factor) from the sector of `from` into the sector
+ * of `to`.  c: HOST [n_sites][2] = (Re, Im) of c_i.  The two sectors have the
+ * same group (the same elements, in any order) and n_up, and O must map one
+ * onto the other: for every element g, s_g c_{g^-1(j)} = lambda(g) c_j for all
+ * sites j (s_g = -1 for an element with spin flip, +1 otherwise), |lambda(g)| = 1,
+ * and chi_to(g) = lambda(g) chi_from(g) (within 1e-9).  With the normalised
+ * projections of Eq. symmetryadaptedwavefunction1d in both sectors,
+ *   y_sigma = f(sigma) x_j,  f(sigma) = sum_i c_i s^z_i(sigma), s^z = +-1/2,
+ * for each representative sigma of `to` at index j of `from` (0 when sigma is
+ * not in `from`'s basis: its projector vanishes there).
+ *   x: DEVICE [nvec][D_from], y: DEVICE [nvec][D_to], `dtype`, caller-owned,
+ *   column-major as for ed_apply, 1 <= nvec <= 8; y is overwritten.
+ * Errors: ED_ERR_ARG for null pointers, sectors that differ in n_sites, n_up
+ * or group, coefficients that are all zero or that violate the condition
+ * above, characters that are not lambda chi, or a real dtype with complex
+ * coefficients or characters.  Runs on `stream` and synchronises it (N
+ * coefficients in device memory from `to`'s allocator). */
+ed_status ed_apply_sz(const ed_basis* from, const ed_basis* to, const double* c, ed_dtype dtype, const void* x,
+                      void* y, int32_t nvec, ed_stream stream);
+
 void ed_basis_free(ed_basis* basis);
 
 /* ed_hamiltonian_create -- bind terms to a basis.
@@ -329,6 +351,25 @@ ed_status ed_expectation(const ed_hamiltonian* h, ed_dtype dtype, const void* x,
  * Workspace (m + 1 vectors) from the basis's allocator.  Synchronous. */
 ed_status ed_time_evolve(const ed_hamiltonian* h, ed_dtype dtype, void* psi, double dt, int32_t m, ed_stream stream,
                          double* err, int32_t* m_used);
+
+/* ed_lanczos_tridiag -- the Lanczos recursion (Eqs. lanczosrecursion, tmatrix)
+ * started from a given DEVICE vector x [D] of `dtype` (not modified, need not
+ * be normalised): v_0 = x/|x|, alpha[n] = <v_n|H v_n>, beta[n] = |w_n| with
+ * w_n = H v_n - alpha[n] v_n - beta[n-1] v_{n-1}, v_{n+1} = w_n/beta[n], for
+ * n < *m_used <= m.  T has diagonal alpha[0..m_used-1] and off-diagonal
+ * beta[0..m_used-2]; beta[m_used-1] is the norm of the last residual.  The
+ * recursion stops early when beta[n] < 1e-14 (|alpha[n]| + 1) (x lies in an
+ * invariant subspace of that dimension).  *norm2 (if non-NULL) = <x|x>.
+ * The continued-fraction expansion <x|(z - H)^-1|x> =
+ * norm2 / (z - alpha[0] - beta[0]^2 / (z - alpha[1] - ...)) of a dynamical
+ * correlation function needs only these numbers.  reorth = 1 keeps all
+ * m+1 vectors (m capped at D) and orthogonalises each new one against them
+ * (classical Gram-Schmidt twice, the second pass against the last two);
+ * reorth = 0 is the plain three-term recursion with three vectors.
+ * alpha, beta: HOST [m].  1 <= m <= 100000.  Workspace from the basis's
+ * allocator; FP64 reductions.  Synchronous. */
+ed_status ed_lanczos_tridiag(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t m, int32_t reorth,
+                             ed_stream stream, double* alpha, double* beta, double* norm2, int32_t* m_used);
 
 /* Lowest k eigenvalues of a Lanczos T-matrix (Eq. tmatrix: diagonal alpha[n],
  * off-diagonal beta[n-1], HOST arrays) by Sturm bisection in FP64, the solver

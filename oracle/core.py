@@ -28,7 +28,9 @@ Large-Scale Exact Diagonalization" and the sections it builds on):
     coefficients in a subgroup's sector -- `restrict`; products of two bond or
     triangle operators -- `product_expectation`; the nematic and chirality
     order parameters (Eqs. nematicorderparameter, chiralityorderparameter)
-    term by term -- `nematic`, `chirality_sum`.
+    term by term -- `nematic`, `chirality_sum`;
+  * the dynamical structure factor of a one-site S^z sum as poles and weights
+    from the dense eigendecomposition -- `sz_spectrum`, `lorentzians`.
 """
 from __future__ import annotations
 
@@ -416,6 +418,29 @@ def chirality_sum(sector, psi: np.ndarray, tri, tris) -> complex:
     nrm = np.vdot(phi, phi)
     u = _apply_local(N, states, idx, phi, tri, M)
     return complex(sum(np.vdot(u, _apply_local(N, states, idx, phi, t, M)) for t in tris) / nrm)
+
+
+def sz_spectrum(problem, psi: np.ndarray, c) -> tuple[np.ndarray, np.ndarray, float]:
+    """(poles E_n - E_0, weights |<n|O|0>|^2, E_0) for O = sum_i c_i S^z_i and
+    the state |0> of `psi` in problem.sector (normalised here), from the
+    eigenvectors of the dense fixed-Sz matrix (`dense_sz`).  The dynamical
+    structure factor is sum_n w_n delta(w - pole_n); E_0 = <0|H|0>.  N <= 14."""
+    phi, states = plain_state(problem.sector, psi)
+    phi = phi / np.linalg.norm(phi)
+    N = sec_N(problem.sector)
+    c = np.asarray(c, dtype=complex)
+    f = np.array([sum(c[i] * (0.5 if (int(s) >> (N - 1 - i)) & 1 else -0.5) for i in range(N)) for s in states])
+    Hd, _ = dense_sz(problem)
+    e0 = float(np.real(np.vdot(phi, Hd @ phi)))
+    w, v = np.linalg.eigh(Hd)
+    amp = v.conj().T @ (f * phi)
+    return w - e0, np.abs(amp) ** 2, e0
+
+
+def lorentzians(poles, weights, omegas, eta: float) -> np.ndarray:
+    """sum_n w_n (eta/pi) / ((w - pole_n)^2 + eta^2) at each frequency w."""
+    om = np.asarray(omegas, dtype=np.float64)[:, None]
+    return (np.asarray(weights)[None, :] * (eta / np.pi) / ((om - np.asarray(poles)[None, :]) ** 2 + eta * eta)).sum(1)
 
 
 def evolve(H, psi: np.ndarray, t: float) -> np.ndarray:

@@ -438,6 +438,165 @@ ed_status restrict_vectors(const ed_basis* from, const ed_basis* to, ed_dtype dt
     return st;
 }
 
+// ---------------------------------------------------------------- one-site S^z sums between sectors
+// O = sum_i c_i S^z_i is diagonal in the product basis.  When every element
+// of the common group G satisfies g O g^-1 = lambda(g) O, O maps the sector
+// of chi into the sector of chi' = lambda chi, and for a representative sigma
+// of the target <sigma~'|O|psi> = f(sigma) x_j with f(sigma) = sum_i c_i s^z_i(sigma)
+// and j the index of sigma in the source basis (the two normalisations
+// sqrt(|G| |Stab(sigma)|) cancel; 0 if sigma's projector vanishes in the source).
+struct SzArgs {
+    const void* reps_from;
+    const uint32_t* dir_base;
+    const uint8_t* dir_q;
+    const uint2* limits;
+    int L;
+    int64_t Df;
+    const void* reps_to;
+    int64_t Dt;
+    int N;
+    const double2* c;           // [N] by bit position (bit N-1-i holds site i)
+    double2 c_sum;              // sum_i c_i
+    const void* x;
+    void* y;
+    int nvec;
+};
+
+template <typename W, int K>
+__global__ void __launch_bounds__(256) sz_kernel(SzArgs a) {
+    using T = typename RVal<K>::T;
+    __shared__ double2 cb[64];
+    for (int b = threadIdx.x; b < 64; b += blockDim.x) cb[b] = b < a.N ? a.c[b] : make_double2(0.0, 0.0);
+    __syncthreads();
+    const W* reps_f = (const W*)a.reps_from;
+    const W* reps_t = (const W*)a.reps_to;
+    const T* x = (const T*)a.x;
+    T* y = (T*)a.y;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.Dt; i += (int64_t)gridDim.x * blockDim.x) {
+        const W s = ld_ro(reps_t + i);
+        int64_t j = find_index<W>(s, reps_f, a.dir_base, a.dir_q, a.limits, a.L);
+        // s need not be in the source basis: confirm a fingerprint hit
+        if (j >= 0 && ld_ro(reps_f + j) != s) j = -1;
+        double2 f = make_double2(-0.5 * a.c_sum.x, -0.5 * a.c_sum.y);
+        W rest = s;
+        while (rest) {
+            const int b = (sizeof(W) == 8) ? __ffsll((long long)rest) - 1 : __ffs((int)(uint32_t)rest) - 1;
+            f.x += cb[b].x;
+            f.y += cb[b].y;
+            rest &= rest - 1;
+        }
+        for (int v = 0; v < a.nvec; ++v)
+            y[(int64_t)v * a.Dt + i] = j >= 0 ? scale_val(f, ld_ro(x + (int64_t)v * a.Df + j)) : zero_val<T>();
+    }
+}
+
+template <typename W, int K>
+static ed_status launch_sz(const SzArgs& a, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>((a.Dt + 255) / 256, (int64_t)sms * 8));
+    sz_kernel<W, K><<<grid, 256, 0, s>>>(a);
+    ED_CUDA(cudaGetLastError());
+    return ED_OK;
+}
+
+// lambda(g) with s_g c_{g^-1(j)} = lambda(g) c_j for all sites j (s_g = -1 for a
+// spin flip), and chi_to(g) = lambda(g) chi_from(g) for the matching element.
+static ed_status sz_check(const HostTables& f, const HostTables& t, const double* c, bool real_kind) {
+    if (f.N != t.N || f.n_up != t.n_up || f.G != t.G) return fail(ED_ERR_ARG, "sectors differ in n_sites, n_up or group order");
+    const int N = f.N;
+    int j0 = 0;
+    double cmax = 0.0;
+    for (int j = 0; j < N; ++j) {
+        const double a = hypot(c[2 * j], c[2 * j + 1]);
+        if (a > cmax) { cmax = a; j0 = j; }
+        if (real_kind && fabs(c[2 * j + 1]) > 1e-12) return fail(ED_ERR_ARG, "complex coefficients need a complex dtype");
+    }
+    if (!(cmax > 0.0)) return fail(ED_ERR_ARG, "all coefficients are zero");
+    std::vector<int> inv(N);
+    for (int e = 0; e < t.G; ++e) {
+        const int32_t* p = t.perm.data() + (size_t)e * N;
+        for (int i = 0; i < N; ++i) inv[p[i]] = i;
+        const double sg = t.flip[e] ? -1.0 : 1.0;
+        // lambda = s_g c_{g^-1(j0)} / c_{j0}
+        const double ar = sg * c[2 * inv[j0]], ai = sg * c[2 * inv[j0] + 1];
+        const double br = c[2 * j0], bi = c[2 * j0 + 1], bb = br * br + bi * bi;
+        const double lr = (ar * br + ai * bi) / bb, li = (ai * br - ar * bi) / bb;
+        if (fabs(lr * lr + li * li - 1.0) > 1e-9) return fail(ED_ERR_ARG, "element %d does not map the operator onto a multiple of itself", e);
+        for (int j = 0; j < N; ++j) {
+            const double er = sg * c[2 * inv[j]] - (lr * c[2 * j] - li * c[2 * j + 1]);
+            const double ei = sg * c[2 * inv[j] + 1] - (lr * c[2 * j + 1] + li * c[2 * j]);
+            if (hypot(er, ei) > 1e-9 * cmax)
+                return fail(ED_ERR_ARG, "element %d does not map the operator onto a multiple of itself", e);
+        }
+        // matching element of the source and its character
+        int m = -1;
+        for (int g = 0; g < f.G && m < 0; ++g)
+            if (f.flip[g] == t.flip[e] && std::equal(p, p + N, f.perm.data() + (size_t)g * N)) m = g;
+        if (m < 0) return fail(ED_ERR_ARG, "element %d of the target group is not in the source group", e);
+        const double xr = lr * f.chi[2 * m] - li * f.chi[2 * m + 1], xi = lr * f.chi[2 * m + 1] + li * f.chi[2 * m];
+        if (hypot(xr - t.chi[2 * e], xi - t.chi[2 * e + 1]) > 1e-9)
+            return fail(ED_ERR_ARG, "target characters are not lambda chi for element %d", e);
+    }
+    return ED_OK;
+}
+
+ed_status sz_transfer(const ed_basis* from, const ed_basis* to, const double* c, ed_dtype dtype, const void* x, void* y,
+                      int nvec, cudaStream_t s) {
+    if (!from || !to || !c || !x || !y) return fail(ED_ERR_ARG, "null argument");
+    if (nvec < 1 || nvec > 8) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    if (dtype != ED_F64 && dtype != ED_F32 && dtype != ED_C128 && dtype != ED_C64) return fail(ED_ERR_ARG, "bad dtype");
+    const bool real_kind = dtype == ED_F64 || dtype == ED_F32;
+    if (real_kind && (!from->ht.real_chars || !to->ht.real_chars))
+        return fail(ED_ERR_ARG, "complex characters need a complex dtype");
+    ed_status st = sz_check(from->ht, to->ht, c, real_kind);
+    if (st != ED_OK) return st;
+    if (to->dim == 0) return ED_OK;
+    const int N = from->ht.N;
+    std::vector<double2> cb(N);
+    double2 csum = make_double2(0.0, 0.0);
+    for (int i = 0; i < N; ++i) {
+        cb[N - 1 - i] = make_double2(c[2 * i], real_kind ? 0.0 : c[2 * i + 1]);
+        csum.x += cb[N - 1 - i].x;
+        csum.y += cb[N - 1 - i].y;
+    }
+    SzArgs a{};
+    a.reps_from = from->reps.p;
+    const uint8_t* dir = (const uint8_t*)from->limits.p;
+    a.dir_base = (const uint32_t*)dir;
+    a.dir_q = dir + from->dir_q_off();
+    a.limits = (const uint2*)(dir + from->dir_lim_off());
+    a.L = from->prefix_bits;
+    a.Df = from->dim;
+    a.reps_to = to->reps.p;
+    a.Dt = to->dim;
+    a.N = N;
+    a.c_sum = csum;
+    a.x = x;
+    a.y = y;
+    a.nvec = nvec;
+    double2* dc = (double2*)to->alloc.get((size_t)N * sizeof(double2), s);
+    if (!dc) return fail(ED_ERR_NOMEM, "coefficient table");
+    a.c = dc;
+    cudaError_t e = cudaMemcpyAsync(dc, cb.data(), (size_t)N * sizeof(double2), cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemcpyAsync");
+    if (st == ED_OK) {
+        const bool w8 = from->word == 8;
+        switch (dtype) {
+            case ED_F64: st = w8 ? launch_sz<uint64_t, 0>(a, s) : launch_sz<uint32_t, 0>(a, s); break;
+            case ED_F32: st = w8 ? launch_sz<uint64_t, 1>(a, s) : launch_sz<uint32_t, 1>(a, s); break;
+            case ED_C128: st = w8 ? launch_sz<uint64_t, 2>(a, s) : launch_sz<uint32_t, 2>(a, s); break;
+            case ED_C64: st = w8 ? launch_sz<uint64_t, 3>(a, s) : launch_sz<uint32_t, 3>(a, s); break;
+        }
+    }
+    // the coefficient table is released once the kernel has run
+    e = cudaStreamSynchronize(s);
+    if (st == ED_OK && e != cudaSuccess) st = cuda_fail(e, "sz transfer");
+    to->alloc.put(dc, (size_t)N * sizeof(double2), s);
+    return st;
+}
+
 // ---------------------------------------------------------------- no-allocation variant
 // Some callers cannot allocate device memory themselves: applications whose
 // device memory is owned by another runtime's pool (a framework that reserves

@@ -401,6 +401,9 @@ namespace ed {
 // ed_basis.cu: restriction of sector vectors to a subgroup's sector.
 ed_status restrict_vectors(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int nvec,
                            cudaStream_t s);
+// ed_basis.cu: one-site S^z sums between sectors.
+ed_status sz_transfer(const ed_basis* from, const ed_basis* to, const double* c, ed_dtype dtype, const void* x, void* y,
+                      int nvec, cudaStream_t s);
 }  // namespace ed
 
 extern "C" {
@@ -508,6 +511,11 @@ ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* st
 ed_status ed_restrict(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int32_t nvec,
                       ed_stream stream) {
     return restrict_vectors(from, to, dtype, x, y, nvec, (cudaStream_t)stream);
+}
+
+ed_status ed_apply_sz(const ed_basis* from, const ed_basis* to, const double* c, ed_dtype dtype, const void* x, void* y,
+                      int32_t nvec, ed_stream stream) {
+    return sz_transfer(from, to, c, dtype, x, y, nvec, (cudaStream_t)stream);
 }
 
 void ed_basis_free(ed_basis* b) {

@@ -989,7 +989,106 @@ static ed_status evolve_kind(const ed_hamiltonian* h, void* psi, double dt, int 
     return ED_OK;
 }
 
+// The Lanczos recursion (Eqs. lanczosrecursion, tmatrix) from a given vector
+// x: v_0 = x/|x|, alpha_n = <v_n|H v_n>, beta_n = |w_n| with
+// w_n = H v_n - alpha_n v_n - beta_{n-1} v_{n-1}, v_{n+1} = w_n / beta_n.  With
+// reorth the m+1 vectors are kept and w_n is orthogonalised against all of them
+// (classical Gram-Schmidt, then again against the last two); without, three
+// vectors live at a time (the continued-fraction expansion needs only T).
+template <int K>
+static ed_status tridiag_kind(const ed_hamiltonian* h, ed_dtype dt, const void* x, int m, bool reorth, cudaStream_t s,
+                              double* alpha, double* beta, double* norm2, int* m_used) {
+    using T = typename LV<K>::T;
+    Lz<K> z;
+    z.h = h;
+    z.b = h->basis;
+    z.s = s;
+    z.D = h->basis->dim;
+    ED_CUDA(cudaDeviceGetAttribute(&z.sms, cudaDevAttrMultiProcessorCount, h->basis->device));
+    const int64_t D = z.D;
+    if (reorth) m = (int)std::min<int64_t>(m, D);
+    const int slots = reorth ? m + 1 : 2;
+    z.nb = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (D + 4095) / 4096));
+    T* V = (T*)z.get((size_t)slots * D * sizeof(T));
+    T* w = (T*)z.get((size_t)D * sizeof(T));
+    double2* partial = (double2*)z.get((size_t)(slots + 2) * z.nb * sizeof(double2));
+    double2* coef = (double2*)z.get((size_t)(slots + 2) * sizeof(double2));
+    double* beta_d = (double*)z.get(2 * sizeof(double));
+    double2* alpha_d = (double2*)z.get(sizeof(double2));
+    if (!V || !w || !partial || !coef || !beta_d || !alpha_d) return fail(ED_ERR_NOMEM, "Lanczos workspace");
+    const unsigned g = z.grid();
+    auto dot = [&](const T* A, int nk, const T* bv, double2* out) {
+        multi_dot<K><<<dim3(z.nb, nk), 256, 0, s>>>(A, D, bv, D, partial);
+        reduce_partials<<<std::min(nk, 1024), 256, 0, s>>>(partial, z.nb, nk, out);
+    };
+    auto slot = [&](int n) { return V + (int64_t)(reorth ? n : (n & 1)) * D; };
+    ED_CUDA(cudaMemcpyAsync(V, x, (size_t)D * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    dot(V, 1, V, coef);
+    double2 n2;
+    ED_CUDA(cudaMemcpyAsync(&n2, coef, sizeof(double2), cudaMemcpyDeviceToHost, s));
+    sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
+    ED_CUDA(cudaStreamSynchronize(s));
+    if (!(n2.x > 0.0)) return fail(ED_ERR_ARG, "the start vector is zero");
+    if (norm2) *norm2 = n2.x;
+    scale_by<K><<<g, 256, 0, s>>>(V, V, D, beta_d);
+    int mm = 0;
+    for (int n = 0; n < m; ++n) {
+        T* vn = slot(n);
+        ed_status st = apply_launch(h, dt, vn, w, 1, s);
+        if (st != ED_OK) return st;
+        dot(vn, 1, w, alpha_d);
+        lanczos_axpy<K><<<g, 256, 0, s>>>(w, vn, n > 0 ? slot(n - 1) : nullptr, D, alpha_d, beta_d);
+        if (reorth) {
+            for (int pass = 0; pass < 2; ++pass) {
+                const int j0 = pass == 0 ? 0 : std::max(0, n - 1);
+                const int nj = n + 1 - j0;
+                dot(V + (int64_t)j0 * D, nj, w, coef);
+                multi_axpy<K><<<g, 256, 0, s>>>(w, V + (int64_t)j0 * D, D, nj, coef, D);
+            }
+        }
+        dot(w, 1, w, coef + slots + 1);
+        sqrt_re<<<1, 1, 0, s>>>(coef + slots + 1, beta_d);
+        double2 ah;
+        double bh;
+        ED_CUDA(cudaMemcpyAsync(&ah, alpha_d, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaMemcpyAsync(&bh, beta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaStreamSynchronize(s));
+        alpha[n] = ah.x;
+        beta[n] = bh;
+        mm = n + 1;
+        // an invariant subspace: T is complete
+        if (bh < 1e-14 * (fabs(ah.x) + 1.0)) break;
+        if (n + 1 < m) scale_by<K><<<g, 256, 0, s>>>(slot(n + 1), w, D, beta_d);
+    }
+    ED_CUDA(cudaGetLastError());
+    ED_CUDA(cudaStreamSynchronize(s));
+    if (m_used) *m_used = mm;
+    return ED_OK;
+}
+
 }  // namespace ed
+
+extern "C" ed_status ed_lanczos_tridiag(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t m,
+                                        int32_t reorth, ed_stream stream, double* alpha, double* beta, double* norm2,
+                                        int32_t* m_used) {
+    using namespace ed;
+    if (!h || !x || !alpha || !beta) return fail(ED_ERR_ARG, "null argument");
+    if (m < 1 || m > 100000) return fail(ED_ERR_ARG, "number of steps out of range [1,100000]");
+    if ((dtype == ED_F64 || dtype == ED_F32) && !h->is_real)
+        return fail(ED_ERR_ARG, "complex Hamiltonian or characters need a complex dtype");
+    cudaStream_t s = (cudaStream_t)stream;
+    int mu = 0;
+    ed_status st;
+    switch (dtype) {
+        case ED_F64: st = tridiag_kind<0>(h, dtype, x, m, reorth != 0, s, alpha, beta, norm2, &mu); break;
+        case ED_F32: st = tridiag_kind<1>(h, dtype, x, m, reorth != 0, s, alpha, beta, norm2, &mu); break;
+        case ED_C128: st = tridiag_kind<2>(h, dtype, x, m, reorth != 0, s, alpha, beta, norm2, &mu); break;
+        case ED_C64: st = tridiag_kind<3>(h, dtype, x, m, reorth != 0, s, alpha, beta, norm2, &mu); break;
+        default: return fail(ED_ERR_ARG, "bad dtype");
+    }
+    if (m_used) *m_used = mu;
+    return st;
+}
 
 extern "C" ed_status ed_time_evolve(const ed_hamiltonian* h, ed_dtype dtype, void* psi, double dt, int32_t m,
                                     ed_stream stream, double* err, int32_t* m_used) {

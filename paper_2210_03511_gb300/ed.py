@@ -107,6 +107,9 @@ def lib():
         L.ed_expectation.argtypes = [c_vp, ctypes.c_int, c_vp, c_i32, c_vp, P(c_dbl)]
         L.ed_time_evolve.argtypes = [c_vp, ctypes.c_int, c_vp, c_dbl, c_i32, c_vp, P(c_dbl), P(c_i32)]
         L.ed_restrict.argtypes = [c_vp, c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
+        L.ed_apply_sz.argtypes = [c_vp, c_vp, P(c_dbl), ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
+        L.ed_lanczos_tridiag.argtypes = [c_vp, ctypes.c_int, c_vp, c_i32, c_i32, c_vp, P(c_dbl), P(c_dbl), P(c_dbl),
+                                         P(c_i32)]
         L.ed_batch_free.argtypes = [c_vp]
         L.ed_batch_free.restype = None
         L.ed_lanczos_batch.argtypes = [c_vp, P(ed_block_lanczos_opts), P(c_dbl), P(ed_block_lanczos_report), c_vp]
@@ -117,7 +120,7 @@ def lib():
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
                   "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation",
-                  "ed_time_evolve", "ed_restrict"):
+                  "ed_time_evolve", "ed_restrict", "ed_apply_sz", "ed_lanczos_tridiag"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -232,6 +235,30 @@ class Basis:
         check(lib().ed_restrict(self.handle, sub.handle, dt, x.data_ptr(), y.data_ptr(), nvec, _stream_handle(stream)))
         return y
 
+    def apply_sz(self, to: "Basis", c, x, y=None, stream=None):
+        """ed_apply_sz: y = (sum_i c_i S^z_i) x from this sector into the sector of
+        `to` (same group; characters multiplied by the operator's phases).  c:
+        complex [n_sites]; x: torch CUDA tensor [D] or [nvec, D].  Returns y."""
+        import torch
+        dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
+        if not x.is_cuda or not x.is_contiguous() or x.shape[-1] != self.dim:
+            raise ValueError("x must be a contiguous CUDA tensor with last dimension = basis dimension")
+        cc = np.asarray(c, dtype=complex)
+        if cc.shape != (self.n_sites,):
+            raise ValueError("c must have one coefficient per site")
+        c2 = np.ascontiguousarray(np.stack([cc.real, cc.imag], axis=1), dtype=np.float64)
+        shape = tuple(x.shape[:-1]) + (to.dim,)
+        if y is None:
+            y = torch.empty(shape, dtype=x.dtype, device=x.device)
+        elif y.dtype != x.dtype or tuple(y.shape) != shape or not y.is_cuda or not y.is_contiguous():
+            raise ValueError("y must be a contiguous CUDA tensor of x's dtype with last dimension = to.dim")
+        nvec = 1 if x.dim() == 1 else x.shape[0]
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        check(lib().ed_apply_sz(self.handle, to.handle, _ptr(c2, c_dbl), dt, x.data_ptr(), y.data_ptr(), nvec,
+                                _stream_handle(stream)))
+        return y
+
     def close(self):
         if self.handle:
             lib().ed_basis_free(self.handle)
@@ -313,6 +340,25 @@ class Hamiltonian:
         if raw:
             return out[:, 0] + 1j * out[:, 1], out[:, 2].copy()
         return (out[:, 0] + 1j * out[:, 1]) / out[:, 2]
+
+    def lanczos_tridiag(self, x, m, reorth=False, stream=None):
+        """ed_lanczos_tridiag: (alpha, beta, <x|x>) of the Lanczos recursion started
+        from the torch CUDA tensor x [D]; len(alpha) = len(beta) = steps taken."""
+        import torch
+        dt = {torch.float64: ED_F64, torch.float32: ED_F32, torch.complex64: ED_C64, torch.complex128: ED_C128}[x.dtype]
+        if not x.is_cuda or not x.is_contiguous() or x.numel() != self.dim:
+            raise ValueError("x must be a contiguous CUDA tensor of the basis dimension")
+        if stream is None:
+            stream = torch.cuda.current_stream(x.device)
+        a = np.zeros(int(m), np.float64)
+        b = np.zeros(int(m), np.float64)
+        n2 = c_dbl()
+        mu = c_i32()
+        check(lib().ed_lanczos_tridiag(self.handle, dt, x.data_ptr(), int(m), 1 if reorth else 0,
+                                       _stream_handle(stream), _ptr(a, c_dbl), _ptr(b, c_dbl), ctypes.byref(n2),
+                                       ctypes.byref(mu)))
+        k = int(mu.value)
+        return a[:k].copy(), b[:k].copy(), float(n2.value)
 
     def autotune(self, x, y, stream=None):
         """ed_apply_autotune on torch CUDA tensors shaped as for apply(); returns blocks per SM."""

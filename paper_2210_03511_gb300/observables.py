@@ -21,6 +21,15 @@ with the translations but not with the point group, so psi is first written in
 the basis of its translation-only sector (ed_restrict, the characters of the
 translations are those of psi's irrep) and B is applied there by the H.x
 kernels.
+
+The dynamical spin structure factor
+S(q, w) = sum_n |<n|S^z(q)|0>|^2 delta(w - (E_n - E_0)), with
+S^z(q) = N^-1/2 sum_i exp(i q.r_i) S^z_i, follows by the continued-fraction
+expansion: phi = S^z(q)|0> is formed in the sector S^z(q) maps the ground
+state into (ed_apply_sz: same group, characters times the operator's phases),
+the Lanczos recursion from phi (ed_lanczos_tridiag) gives T, and
+<phi|(z - H)^-1|phi> = |phi|^2 / (z - a_0 - b_0^2 / (z - a_1 - ...)), so that
+S(q, w) = -Im G(w + E_0 + i eta) / pi, a sum of Lorentzians of width eta.
 """
 from __future__ import annotations
 
@@ -198,3 +207,55 @@ def chirality_correlation(ts: TranslationSector, psi, tri, stream=None) -> float
     terms = _Bonds(np.zeros((0, 2), np.int32), np.zeros(0), tris, np.ones(len(tris)))
     _, x2 = ts.moments(psi, terms, stream=stream)
     return x2 / ts.n_trans
+
+
+# ---------------------------------------------------------------- dynamical structure factor
+def szq_coefficients(positions, q) -> np.ndarray:
+    """c_i = exp(i q.r_i) / sqrt(N): the site coefficients of S^z(q)."""
+    r = np.asarray(positions, dtype=np.float64)
+    return np.exp(1j * (r @ np.asarray(q, dtype=np.float64))) / np.sqrt(len(r))
+
+
+def sz_target_sector(sector, c) -> SubSector:
+    """The sector O = sum_i c_i S^z_i maps `sector` into: the same group, with
+    characters lambda(g) chi(g), where s_g c_{g^-1(j)} = lambda(g) c_j (s_g = -1
+    for an element with spin flip).  Raises if O is not mapped onto a multiple
+    of itself by every element (e.g. a momentum not allowed on the torus)."""
+    c = np.asarray(c, dtype=complex)
+    perm = np.asarray(sector.perm, dtype=np.int64)
+    N = perm.shape[1]
+    j0 = int(np.argmax(np.abs(c)))
+    lam = np.empty(len(perm), dtype=complex)
+    for g, p in enumerate(perm):
+        inv = np.empty(N, dtype=np.int64)
+        inv[p] = np.arange(N)
+        sg = -1.0 if np.asarray(sector.spinflip)[g] else 1.0
+        lam[g] = sg * c[inv[j0]] / c[j0]
+        if not np.allclose(sg * c[inv], lam[g] * c, atol=1e-9 * np.abs(c).max()):
+            raise ValueError(f"element {g} does not map the operator onto a multiple of itself")
+    chi = lam * np.asarray(sector.chi, dtype=complex)
+    # exact roots of unity stay exact (real sectors keep real characters)
+    chi = np.where(np.abs(chi.imag) < 1e-12, chi.real + 0j, chi)
+    chi = np.where(np.abs(chi.real) < 1e-12, 1j * chi.imag, chi)
+    return SubSector(int(sector.n_sites), int(sector.n_up), np.asarray(sector.perm, dtype=np.int32),
+                     np.asarray(sector.spinflip, dtype=np.uint8), chi, int(sector.n_sublat))
+
+
+def continued_fraction(alpha, beta, norm2, z) -> np.ndarray:
+    """norm2 / (z - a_0 - b_0^2 / (z - a_1 - ... / (z - a_{m-1}))) for each z."""
+    z = np.atleast_1d(np.asarray(z, dtype=complex))
+    a = np.asarray(alpha, dtype=np.float64)
+    b = np.asarray(beta, dtype=np.float64)
+    d = z - a[-1]
+    for n in range(len(a) - 2, -1, -1):
+        d = z - a[n] - b[n] ** 2 / d
+    return norm2 / d
+
+
+def dynamical_structure_factor(h_target, phi, omegas, e0, eta, m=200, reorth=False, stream=None):
+    """S(q, w) at the frequencies `omegas` with Lorentzian width eta, from
+    phi = S^z(q)|0> in the target sector of the Hamiltonian h_target and the
+    ground-state energy e0.  Returns (S, alpha, beta, |phi|^2)."""
+    a, b, n2 = h_target.lanczos_tridiag(phi, m, reorth=reorth, stream=stream)
+    G = continued_fraction(a, b, n2, np.asarray(omegas, dtype=np.float64) + e0 + 1j * eta)
+    return -G.imag / np.pi, a, b, n2
