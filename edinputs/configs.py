@@ -53,14 +53,15 @@ def triangular(P, J1=1.0, J2=0.0, *, k=(0.0, 0.0), irrep="A1", point="full", spi
                          translations=translations)
 
 
-def kagome(P, J1=1.0, J2=0.0, Jchi=0.0, *, k=(0.0, 0.0), irrep="A", point="rot", spinflip=None,
+def kagome(P, J1=1.0, J2=0.0, Jchi=0.0, *, J3=0.0, k=(0.0, 0.0), irrep="A", point="rot", spinflip=None,
            n_up=None, n_sublat=None, max_table_bytes=96 * 1024, translations=True):
-    """Kagome cluster; the scalar chirality breaks mirrors, so the default point group is C6."""
+    """Kagome cluster (Eq. chiralhamiltonian: J1, J2, J3 across the hexagons, J_chi on
+    every triangle); the scalar chirality breaks mirrors, so the default point group is C6."""
     cl = Cluster(kagome_lattice(), P)
     J = {1: J1}
     if J2:
         J[2] = J2
-    return build_problem(f"kagome{cl.N}", cl, J=J, Jchi=Jchi, n_up=n_up, point=point, k=k, irrep=irrep,
+    return build_problem(f"kagome{cl.N}", cl, J=J, Jchi=Jchi, J3_hex=J3, n_up=n_up, point=point, k=k, irrep=irrep,
                          spinflip=spinflip, n_sublat=n_sublat, max_table_bytes=max_table_bytes,
                          translations=translations)
 

@@ -200,6 +200,29 @@ class Cluster:
                     out.append((i, j))
         return out
 
+    def bonds_across_hexagons(self):
+        """Kagome third neighbours across the hexagons (Eq. chiralhamiltonian's
+        J3 term): pairs at twice the nearest-neighbour distance whose midpoint
+        is a hexagon centre, not a site (the other pairs at that distance run
+        along a line of sites through their middle site)."""
+        shells, disp = self.neighbour_shells(1)
+        d1 = shells[0]
+        out = []
+        for i, (c, s) in enumerate(self.site_list):
+            for L, d in disp[s]:
+                if abs(L - 2 * d1) > 1e-6:
+                    continue
+                if self.locate(self.pos[i] + d / 2) is not None:
+                    continue
+                j = self.locate(self.pos[i] + d)
+                if j is None:
+                    raise RuntimeError("neighbour not on lattice")
+                if j == i:
+                    raise ValueError("cluster too small: bond maps a site onto itself")
+                if i < j:
+                    out.append((i, j))
+        return out
+
     def triangles(self):
         """Elementary nearest-neighbour triangles, vertices counter-clockwise."""
         shells, disp = self.neighbour_shells(1)
@@ -583,13 +606,14 @@ def _snap_roots(chi: np.ndarray) -> np.ndarray:
     return np.array([complex(snap(z.real), snap(z.imag)) for z in np.asarray(chi, dtype=complex)])
 
 
-def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: int | None = None,
+def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, J3_hex: float = 0.0, n_up: int | None = None,
                   point: str = "full", translations: bool = True, k=(0.0, 0.0), irrep: str = "A1",
                   spinflip: int | None = None, max_table_bytes: int = 96 * 1024,
                   n_sublat: int | None = None) -> Problem:
     """Assemble a sector of a cluster.
 
-    J: {shell: coupling}.  k: Cartesian momentum.  irrep: name of a 1-D irrep
+    J: {shell: coupling}.  J3_hex: coupling of the kagome third neighbours
+    across the hexagons.  k: Cartesian momentum.  irrep: name of a 1-D irrep
     of the little group of k.  spinflip: None (no flip), +1 (even), -1 (odd).
     """
     N = cl.N
@@ -638,6 +662,10 @@ def build_problem(name: str, cl: Cluster, *, J: dict, Jchi: float = 0.0, n_up: i
         for b in cl.bonds(shell):
             bonds.append(b)
             Js.append(Jv)
+    if J3_hex != 0.0:
+        for b in cl.bonds_across_hexagons():
+            bonds.append(b)
+            Js.append(J3_hex)
     tris, Jc = [], []
     if Jchi != 0.0:
         for t in cl.triangles():
