@@ -326,3 +326,42 @@ def test_gpu_sum_rules_triangular24(P):
         ht.close()
         bt.close()
     ts.close()
+
+
+# ---------------------------------------------------------------- host logic (CPU)
+def test_continued_fraction_is_the_resolvent():
+    """norm2 / (z - a0 - b0^2/(z - a1 - ...)) = norm2 [(z - T)^-1]_00 for the tridiagonal T."""
+    from paper_2210_03511_gb300.observables import continued_fraction
+    rng = np.random.default_rng(4)
+    for m in (1, 2, 7, 30):
+        a = rng.normal(size=m)
+        b = np.abs(rng.normal(size=m)) + 0.1
+        T = np.diag(a) + np.diag(b[:m - 1], 1) + np.diag(b[:m - 1], -1)
+        z = np.array([0.3 + 0.05j, -1.7 + 0.2j, 4.0 + 1e-3j])
+        G = continued_fraction(a, b, 2.5, z)
+        ref = [2.5 * np.linalg.inv(zz * np.eye(m) - T)[0, 0] for zz in z]
+        assert np.allclose(G, ref, rtol=1e-10, atol=0)
+
+
+def test_sz_target_sector_host():
+    """The target sector of S^z(q) on a ring: characters exp(i (k - q) t); a phase
+    pattern that is not a momentum of the ring is refused."""
+    from paper_2210_03511_gb300.observables import sz_target_sector, szq_coefficients
+    p = _chain(k=1)
+    pos = np.asarray(p.meta["positions"])
+    q = _qchain(5)
+    c = szq_coefficients(pos, q)
+    assert np.allclose(c, _coef(pos, q))
+    tgt = sz_target_sector(p.sector, c)
+    ref = _chain(k=(1 - 5) % 12)
+    assert np.array_equal(np.asarray(tgt.perm), np.asarray(ref.sector.perm))
+    assert np.allclose(tgt.chi, ref.sector.chi, atol=1e-12)
+    assert np.allclose(tgt.chi, _target(p.sector, c).chi, atol=1e-12)
+    with pytest.raises(ValueError):
+        sz_target_sector(p.sector, np.exp(1j * 0.37 * np.arange(12)))
+    # spin flip: S^z changes the flip parity
+    pf = _chain(spinflip=1)
+    tf = sz_target_sector(pf.sector, np.real(_coef(pf.meta["positions"], _qchain(6))).astype(complex))
+    perm = np.asarray(pf.sector.perm)
+    g = [e for e in range(len(perm)) if pf.sector.spinflip[e] and np.array_equal(perm[e], np.arange(12))][0]
+    assert tf.chi[g] == pytest.approx(-pf.sector.chi[g])

@@ -272,3 +272,38 @@ def test_gpu_order_parameters_triangular24_properties(P):
     assert chirality_correlation(ts, psi, tuple(p.meta["triangles"][0])) >= 0.0
     ht.close()
     ts.close()
+
+
+# ---------------------------------------------------------------- host logic (CPU)
+def test_subgroup_sector_host():
+    """The subgroup sector keeps the identity first, the restricted characters
+    and the sublattice blocks; a subgroup without the identity is refused."""
+    from paper_2210_03511_gb300.observables import subgroup_sector
+    p = C.kagome([[2, 0], [0, 2]], 1.0, 0.2, 0.3, irrep="E1")
+    tr = p.meta["translations"]
+    sub = subgroup_sector(p.sector, list(reversed(tr)))
+    assert np.array_equal(sub.perm[0], np.arange(p.sector.n_sites))
+    assert sorted(map(tuple, sub.perm.tolist())) == sorted(tuple(p.sector.perm[t].tolist()) for t in tr)
+    for g, row in enumerate(sub.perm):
+        e = [t for t in tr if np.array_equal(p.sector.perm[t], row)][0]
+        assert sub.chi[g] == p.sector.chi[e] and sub.spinflip[g] == p.sector.spinflip[e]
+    assert sub.n_sublat == p.sector.n_sublat
+    with pytest.raises(ValueError):
+        subgroup_sector(p.sector, [t for t in tr if t != 0])
+
+
+def test_translation_elements_form_the_translation_group():
+    """meta["translations"] of each workload: |T| = number of unit cells, closed
+    under composition, no spin flips, each a fixed-point-free permutation but the
+    identity."""
+    for p in (_tri12(), C.triangular24(), C.kagome36(), C.square32()):
+        tr = p.meta["translations"]
+        perm = np.asarray(p.sector.perm)
+        assert len(tr) == p.meta["n_cells"]
+        rows = {tuple(perm[t].tolist()) for t in tr}
+        for a in tr:
+            assert not p.sector.spinflip[a]
+            if a != 0:
+                assert np.all(perm[a] != np.arange(len(perm[a])))
+            for b in tr:
+                assert tuple(perm[a][perm[b]].tolist()) in rows
