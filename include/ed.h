@@ -366,7 +366,7 @@ ed_status ed_time_evolve(const ed_hamiltonian* h, ed_dtype dtype, void* psi, dou
  * m+1 vectors (m capped at D) and orthogonalises each new one against them
  * (classical Gram-Schmidt twice, the second pass against the last two);
  * reorth = 0 is the plain three-term recursion with three vectors.
- * alpha, beta: HOST [m].  1 <= m <= 100000.  Workspace from the basis's
+ * alpha, beta: HOST [m].  1 <= m <= 100000 (m <= 65534 with reorth).  Workspace from the basis's
  * allocator; FP64 reductions.  Synchronous. */
 ed_status ed_lanczos_tridiag(const ed_hamiltonian* h, ed_dtype dtype, const void* x, int32_t m, int32_t reorth,
                              ed_stream stream, double* alpha, double* beta, double* norm2, int32_t* m_used);

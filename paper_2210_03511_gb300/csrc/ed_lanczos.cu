@@ -1074,6 +1074,8 @@ extern "C" ed_status ed_lanczos_tridiag(const ed_hamiltonian* h, ed_dtype dtype,
     using namespace ed;
     if (!h || !x || !alpha || !beta) return fail(ED_ERR_ARG, "null argument");
     if (m < 1 || m > 100000) return fail(ED_ERR_ARG, "number of steps out of range [1,100000]");
+    // the Gram-Schmidt dot products run one grid row per stored vector
+    if (reorth && m > 65534) return fail(ED_ERR_ARG, "reorthogonalisation needs m <= 65534");
     if ((dtype == ED_F64 || dtype == ED_F32) && !h->is_real)
         return fail(ED_ERR_ARG, "complex Hamiltonian or characters need a complex dtype");
     cudaStream_t s = (cudaStream_t)stream;
