@@ -8,5 +8,6 @@ closed forms, the thesis's worked examples, invariants and brute force.
 """
 from .core import (apply, basis, binom, build, chirality_sum, correlation_matrix, csr, dense_sz, evolve,  # noqa: F401
                    lowest_eigs, nematic, num_threads, plain_state, product_expectation, projector_matrix, rep,
-                   restrict, rows, sector_dim_formula, sz_spectrum, sz_states, triangle_expectation, lorentzians)
+                   restrict, rows, sector_dim_formula, set_num_threads, sz_spectrum, sz_states,
+                   triangle_expectation, lorentzians)
 from .ops import bond_matrix, chirality_matrix  # noqa: F401

@@ -81,6 +81,8 @@ def lib():
                                ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double),
                                P(ctypes.c_uint64), ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, P(ctypes.c_double)]
         L.orc_num_threads.restype = ctypes.c_int
+        L.orc_set_num_threads.restype = None
+        L.orc_set_num_threads.argtypes = [ctypes.c_int]
         _lib = L
     return _lib
 
@@ -181,6 +183,11 @@ def rows(problem, states: np.ndarray, seed: int, is_complex: bool) -> np.ndarray
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the C routines from now on."""
+    lib().orc_set_num_threads(int(n))
 
 
 # --------------------------------------------------------------------------

@@ -274,3 +274,13 @@ int orc_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Threads for the following parallel regions (n >= 1); for the baseline's
+ * single-thread figure. */
+void orc_set_num_threads(int n) {
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
