@@ -18,6 +18,7 @@
 
 #include "ed_device.cuh"
 #include "ed_internal.h"
+#include "ed_transfer.h"
 
 namespace ed {
 

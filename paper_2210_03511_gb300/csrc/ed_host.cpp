@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "ed_internal.h"
+#include "ed_transfer.h"
 
 namespace ed {
 
@@ -397,15 +398,6 @@ static ed_status prepare_terms(const ed_basis* b, const ed_terms* tm, ed_hamilto
 using namespace ed;
 
 // ------------------------------------------------------------------ C ABI
-namespace ed {
-// ed_basis.cu: restriction of sector vectors to a subgroup's sector.
-ed_status restrict_vectors(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int nvec,
-                           cudaStream_t s);
-// ed_basis.cu: one-site S^z sums between sectors.
-ed_status sz_transfer(const ed_basis* from, const ed_basis* to, const double* c, ed_dtype dtype, const void* x, void* y,
-                      int nvec, cudaStream_t s);
-}  // namespace ed
-
 extern "C" {
 
 const char* ed_last_error(void) { return g_err.c_str(); }
