@@ -257,6 +257,45 @@ void ed_hamiltonian_free(ed_hamiltonian* h);
  * Asynchronous on `stream`. */
 ed_status ed_apply(const ed_hamiltonian* h, ed_dtype dtype, const void* x, void* y, int32_t nvec, ed_stream stream);
 
+/* ed_hamiltonian_store -- compute H's sparsity structure once and keep it on
+ * the device, so that later ed_apply calls (and everything built on them:
+ * ed_lanczos, ed_expectation, ed_time_evolve, ed_lanczos_tridiag) stream it
+ * instead of repeating the representative search (Alg. "Sublattice coding
+ * algorithm for finding the representative") and the Limits + binary search
+ * for every element.  The thesis recomputes elements in every
+ * matrix-vector multiply because its sectors (D ~ 10^11) leave no room for the
+ * matrix; sectors that fit one GPU usually leave room for it, and H stays the
+ * same across all Lanczos steps.  What is stored: for every row sigma_i and
+ * every non-zero off-diagonal element of the pull form y_i = sum_j conj(H_ji) x_j
+ * (same elements, same order as the matrix-free kernel), the column j and a
+ * one-byte code of conj(h) chi(g_tau) sqrt(|Stab tau~|); per row the Ising
+ * part (FP64); the coefficients of at most 256 codes.  Columns are cut into
+ * segments of 2^seg_log2 elements and ed_apply runs one pass per segment, so
+ * each pass gathers x from one slice of about the size of L2.  seg_log2 = 0
+ * picks 128 MB of `dtype` elements, at most 2^24; otherwise 5 <= seg_log2 <= 28,
+ * with at most 128 segments, and a stored element keeps its code in the bits
+ * above the column offset (ED_ERR_TABLE_TOO_LARGE if the codes that occur do
+ * not fit beside a seg_log2-bit offset).  Results of
+ * ed_apply are the same H x up to the summation order across segments; with
+ * one segment and real vectors they are bit-identical to the matrix-free
+ * kernel's.  Device memory (about 4 bytes per element plus 9 bytes per row
+ * per segment... exactly *bytes) comes from the basis's allocator; if the
+ * structure would need more than max_bytes, nothing is kept and
+ * ED_ERR_NOMEM is returned (ed_apply stays matrix-free).  Also
+ * ED_ERR_TABLE_TOO_LARGE when more than 256 distinct coefficients occur,
+ * ED_ERR_ARG for more than 255 flip terms.  Synchronous on `stream`.
+ * A second call replaces the stored structure. */
+ed_status ed_hamiltonian_store(ed_hamiltonian* h, ed_dtype dtype, int32_t seg_log2, size_t max_bytes,
+                               ed_stream stream, size_t* bytes);
+
+/* Size of the stored structure: entries (off-diagonal elements), column
+ * segments, distinct coefficient codes, device bytes; all 0 when none. */
+ed_status ed_hamiltonian_store_info(const ed_hamiltonian* h, int64_t* entries, int32_t* segments, int32_t* codes,
+                                    size_t* bytes);
+
+/* Release the stored structure (ed_apply becomes matrix-free again). */
+void ed_hamiltonian_store_free(ed_hamiltonian* h);
+
 /* Counters of the most recent ed_apply on this Hamiltonian (synchronises stream):
  * number of off-diagonal terms whose representative was found (gathers per
  * vector) and number of images skipped as incompatible. */

@@ -6,7 +6,7 @@ import this package.  It shares no code with the CUDA library
 `edinputs`.  Every function is pinned by tests/test_oracle_*.py against
 closed forms, the thesis's worked examples, invariants and brute force.
 """
-from .core import (apply, basis, binom, build, chirality_sum, correlation_matrix, csr, dense_sz, evolve,  # noqa: F401
+from .core import (apply, basis, binom, build, chirality_sum, correlation_matrix, csr, csr_chunked, dense_sz, evolve,  # noqa: F401
                    lowest_eigs, nematic, num_threads, plain_state, product_expectation, projector_matrix, rep,
                    restrict, rows, sector_dim_formula, set_num_threads, sz_spectrum, sz_states,
                    triangle_expectation, lorentzians)

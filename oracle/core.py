@@ -13,7 +13,8 @@ Large-Scale Exact Diagonalization" and the sections it builds on):
     (Alg. "Preparation of the distributed and symmetrized Hilbert space"
     without the distribution) -- `basis`;
   * the sparse matrix in that basis from local operators via
-    Eq. matrixelementrepresentatives_lsed with the conj(chi) reading -- `csr`;
+    Eq. matrixelementrepresentatives_lsed with the conj(chi) reading -- `csr`,
+    or by column ranges on several threads for large sectors -- `csr_chunked`;
   * the dense matrix in the unsymmetrized fixed-Sz space -- `dense_sz`;
   * explicit symmetric vectors by the projector -- `projector_matrix`;
   * sector dimensions by the character formula (Eq. characterformula) --
@@ -76,6 +77,12 @@ def lib():
                               P(ctypes.c_uint64), P(ctypes.c_int32), ctypes.c_int64,
                               ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double),
                               P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_double), ctypes.c_int64]
+        L.orc_coo_cols.restype = ctypes.c_int64
+        L.orc_coo_cols.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_uint8),
+                                   P(ctypes.c_double), P(ctypes.c_uint64), P(ctypes.c_int32), ctypes.c_int64,
+                                   ctypes.c_int64, ctypes.c_int64,
+                                   ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double),
+                                   P(ctypes.c_int64), P(ctypes.c_int64), P(ctypes.c_double), ctypes.c_int64]
         L.orc_rows.restype = None
         L.orc_rows.argtypes = [ctypes.c_int, ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_uint8), P(ctypes.c_double),
                                ctypes.c_int, P(ctypes.c_int32), P(ctypes.c_int32), P(ctypes.c_double),
@@ -167,6 +174,52 @@ def csr(problem, reps=None, stab=None) -> sp.csr_matrix:
     H = sp.coo_matrix((v, (rows[:n], cols[:n])), shape=(D, D)).tocsr()
     H.sum_duplicates()
     return H
+
+
+def csr_chunked(problem, reps=None, stab=None, chunk: int = 8192, workers: int | None = None,
+                real: bool = False):
+    """The matrix of `csr`, assembled by independent column ranges on several
+    host threads (each range is the same column-wise assembly; duplicates are
+    summed per range).  For sectors of millions of states.  Returned in CSC
+    form (the columns are what is assembled); H is Hermitian, so H.T.conj()
+    is the same matrix.  real=True keeps the real part only (for a real
+    Hamiltonian in a sector with real characters; the imaginary parts are
+    checked to be zero)."""
+    from concurrent.futures import ThreadPoolExecutor
+    sec, terms = problem.sector, problem.terms
+    if reps is None:
+        reps, stab = basis(sec)
+    s = _Sec(sec)
+    T, nloc, sites, mats = _terms_c(terms)
+    D = len(reps)
+    reps = np.ascontiguousarray(reps, dtype=np.uint64)
+    stab = np.ascontiguousarray(stab, dtype=np.int32)
+    per_col = int(sum(1 << int(n) for n in nloc))  # at most one entry per local image
+    L = lib()
+
+    def part(c0):
+        c1 = min(D, c0 + chunk)
+        cap = per_col * (c1 - c0)
+        rows = np.empty(max(cap, 1), dtype=np.int64)
+        cols = np.empty(max(cap, 1), dtype=np.int64)
+        vals = np.empty((max(cap, 1), 2), dtype=np.float64)
+        n = L.orc_coo_cols(*s.args(), _p(reps, ctypes.c_uint64), _p(stab, ctypes.c_int32), D, c0, c1, T,
+                           _p(nloc, ctypes.c_int32), _p(sites, ctypes.c_int32), _p(mats, ctypes.c_double),
+                           _p(rows, ctypes.c_int64), _p(cols, ctypes.c_int64), _p(vals, ctypes.c_double), cap)
+        assert n >= 0
+        if real:
+            assert np.all(vals[:n, 1] == 0.0)
+            v = vals[:n, 0].copy()
+        else:
+            v = vals[:n, 0] + 1j * vals[:n, 1]
+        M = sp.coo_matrix((v, (rows[:n], cols[:n] - c0)), shape=(D, c1 - c0)).tocsc()
+        M.sum_duplicates()
+        return M
+
+    workers = workers or os.cpu_count() or 1
+    with ThreadPoolExecutor(workers) as ex:
+        parts = list(ex.map(part, range(0, D, chunk)))
+    return sp.hstack(parts, format="csc")
 
 
 def rows(problem, states: np.ndarray, seed: int, is_complex: bool) -> np.ndarray:

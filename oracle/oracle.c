@@ -172,14 +172,14 @@ static uint64_t local_set(uint64_t s, int N, int nloc, const int32_t* sites, int
 /* Column-wise assembly of the symmetric-basis matrix in COO form:
  * for column sigma~ and every term, every local image tau contributes
  * M[a'][a] * conj(chi(g_tau)) * sqrt(stab_tau / stab_sigma) at row tau~.
- * Entries are emitted unsummed.  Returns the number of entries or -1 if
- * `cap` is too small.  With rows==NULL only counts. */
-int64_t orc_coo(int N, int G, const int32_t* perm, const uint8_t* flip, const double* chi,
-                const uint64_t* reps, const int32_t* stab, int64_t D,
-                int T, const int32_t* nloc, const int32_t* sites, const double* mats,
-                int64_t* rows, int64_t* cols, double* vals, int64_t cap) {
+ * Entries are emitted unsummed, for the columns c0 <= c < c1.  Returns the
+ * number of entries or -1 if `cap` is too small.  With rows==NULL only counts. */
+int64_t orc_coo_cols(int N, int G, const int32_t* perm, const uint8_t* flip, const double* chi,
+                     const uint64_t* reps, const int32_t* stab, int64_t D, int64_t c0, int64_t c1,
+                     int T, const int32_t* nloc, const int32_t* sites, const double* mats,
+                     int64_t* rows, int64_t* cols, double* vals, int64_t cap) {
     int64_t n = 0;
-    for (int64_t c = 0; c < D; ++c) {
+    for (int64_t c = c0; c < c1; ++c) {
         uint64_t s = reps[c];
         for (int t = 0; t < T; ++t) {
             int nl = nloc[t];
@@ -210,6 +210,15 @@ int64_t orc_coo(int N, int G, const int32_t* perm, const uint8_t* flip, const do
         }
     }
     return n;
+}
+
+/* The whole matrix: columns 0..D-1 (orc_coo_cols restricted to a column
+ * range lets independent ranges be assembled concurrently). */
+int64_t orc_coo(int N, int G, const int32_t* perm, const uint8_t* flip, const double* chi,
+                const uint64_t* reps, const int32_t* stab, int64_t D,
+                int T, const int32_t* nloc, const int32_t* sites, const double* mats,
+                int64_t* rows, int64_t* cols, double* vals, int64_t cap) {
+    return orc_coo_cols(N, G, perm, flip, chi, reps, stab, D, 0, D, T, nloc, sites, mats, rows, cols, vals, cap);
 }
 
 /* SplitMix64 finaliser and the keyed uniform used for sampled vectors. */

@@ -99,7 +99,9 @@ ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s) {
     return fail(ED_ERR_ARG, "bad dtype");
 }
 
-ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s) {
+ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s,
+                       bool use_cache) {
+    if (use_cache && h->cache.valid) return cache_apply(h, dt, x, y, nvec, s);
     const ed_basis* b = h->basis;
     if (h->n_flip > 256) return fail(ED_ERR_ARG, "more than 256 flip terms are not supported");
     HxArgs a = make_args(h);
@@ -140,10 +142,10 @@ extern "C" ed_status ed_apply_autotune(ed_hamiltonian* h, ed_dtype dtype, const 
     ed_status st = ED_OK;
     for (int b = 1; b <= top && st == ED_OK; ++b) {
         slot = b;
-        st = apply_launch(h, dtype, x, y, nvec, s);  // warm-up (configures the instantiation)
+        st = apply_launch(h, dtype, x, y, nvec, s, false);  // warm-up (configures the instantiation)
         if (st != ED_OK) break;
         if (cudaEventRecord(e0, s) != cudaSuccess) { st = fail(ED_ERR_CUDA, "event record"); break; }
-        st = apply_launch(h, dtype, x, y, nvec, s);
+        st = apply_launch(h, dtype, x, y, nvec, s, false);
         if (st != ED_OK) break;
         if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
             st = fail(ED_ERR_CUDA, "event wait");

@@ -188,6 +188,30 @@ __global__ void scan_tile_apply(const uint32_t* in, uint64_t n, const uint64_t* 
         }
 }
 
+// Exclusive scan of n u32 values into u64 offsets (device), total to the host.
+ed_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* total, const Alloc& A,
+                             cudaStream_t s) {
+    const uint64_t n_tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const size_t bytes = (size_t)(n_tiles + 2) * 8;
+    uint64_t* tiles = (uint64_t*)A.get(bytes, s);
+    if (!tiles) return fail(ED_ERR_NOMEM, "scan scratch");
+    uint64_t* d_total = tiles + n_tiles + 1;
+    ed_status st = ED_OK;
+    if (n_tiles) {
+        scan_tile_sums<<<(unsigned)n_tiles, 256, 0, s>>>(in, n, tiles);
+        scan_tiles_serial<<<1, 1024, 0, s>>>(tiles, n_tiles, d_total);
+        scan_tile_apply<<<(unsigned)n_tiles, 256, 0, s>>>(in, n, tiles, out);
+    } else {
+        cudaMemsetAsync(d_total, 0, 8, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(total, d_total, 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "exclusive scan");
+    A.put(tiles, bytes, s);
+    return st;
+}
+
 // ---------------------------------------------------------------- Limits
 // Two-level Limits: for top-block value v, bucket b = next q_v bits;
 // key = base_v + b; limits[key] = first index with state >= (v, b).

@@ -561,6 +561,7 @@ ed_status ed_hamiltonian_is_real(const ed_hamiltonian* h, int32_t* is_real) {
 
 void ed_hamiltonian_free(ed_hamiltonian* h) {
     if (!h) return;
+    cache_free(h);
     const Alloc& A = h->basis->alloc;
     A.put(h->d_flips.p, h->d_flips.bytes, 0);
     A.put(h->d_diag_pos.p, h->d_diag_pos.bytes, 0);

@@ -132,6 +132,21 @@ struct ed_basis {
     size_t dir_lim_off() const { return (dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15) + 15) & ~(size_t)15; }
 };
 
+namespace ed {
+// Stored structure of H (csrc/ed_cache.cu): per column segment b, entry
+// counts per row, per-slice offsets and the entries (code << 24 | column
+// offset), the per-row Ising part, and the coefficient table of the codes.
+struct HCache {
+    bool valid = false;
+    int seg_bits = 0, nb = 0, n_code = 0, sms = 0, off_bits = 24;
+    int64_t ns = 0;                 // slices of 32 rows
+    DevBuf counts, boff, ent, diag, ctab, ctr;
+    std::vector<uint64_t> bbase;    // [nb+1] first entry of each segment
+    uint64_t n_ent = 0, n_skip = 0;
+    size_t bytes = 0;
+};
+}  // namespace ed
+
 struct ed_hamiltonian {
     const ed_basis* basis = nullptr;
     bool is_real = true;
@@ -148,6 +163,7 @@ struct ed_hamiltonian {
     std::vector<uint8_t> jcls;          // [n_flip]
     ed::DevBuf d_jhs, d_jcls;
     int tuned_blocks[4][2] = {};        // resident H.x blocks per SM by dtype, nvec == 1 / > 1 (0: default)
+    ed::HCache cache;                   // stored structure, when built (ed_hamiltonian_store)
 };
 
 namespace ed {
@@ -207,8 +223,15 @@ ed_status representatives_device(const ed_basis* b, const uint64_t* states, int6
                                  int32_t* nstab, uint8_t* compat, cudaStream_t s);
 ed_status representatives_static(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
                                  int32_t* nstab, uint8_t* compat, cudaStream_t s);
-// implemented in ed_apply.cu
-ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
+ed_status exclusive_scan_u32(const uint32_t* in, uint64_t n, uint64_t* out, uint64_t* total, const Alloc& A,
+                             cudaStream_t s);
+// implemented in ed_apply.cu; uses the stored structure when there is one and use_cache is set
+ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s,
+                       bool use_cache = true);
+// implemented in ed_cache.cu
+ed_status cache_build(ed_hamiltonian* h, ed_dtype dtype, int seg_log2, size_t max_bytes, cudaStream_t s);
+ed_status cache_apply(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s);
+void cache_free(ed_hamiltonian* h);
 // implemented in ed_lanczos.cu
 void tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b, int n, int k, bool filter,
                     double eps_v, std::vector<double>& lam);

@@ -96,6 +96,10 @@ def lib():
         L.ed_hamiltonian_free.restype = None
         L.ed_apply.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
         L.ed_apply_counters.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
+        L.ed_hamiltonian_store.argtypes = [c_vp, ctypes.c_int, c_i32, ctypes.c_size_t, c_vp, P(ctypes.c_size_t)]
+        L.ed_hamiltonian_store_info.argtypes = [c_vp, P(c_i64), P(c_i32), P(c_i32), P(ctypes.c_size_t)]
+        L.ed_hamiltonian_store_free.argtypes = [c_vp]
+        L.ed_hamiltonian_store_free.restype = None
         L.ed_lanczos.argtypes = [c_vp, P(ed_lanczos_opts), P(c_dbl), c_vp, P(ed_lanczos_report), c_vp]
         L.ed_batch_create.argtypes = [P(c_vp), c_i32, P(c_vp)]
         L.ed_batch_rows.argtypes = [c_vp, P(c_i64)]
@@ -120,7 +124,8 @@ def lib():
         for f in ("ed_basis_build", "ed_basis_dim", "ed_basis_export", "ed_sector_tables", "ed_hamiltonian_create",
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
                   "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation",
-                  "ed_time_evolve", "ed_restrict", "ed_apply_sz", "ed_lanczos_tridiag"):
+                  "ed_time_evolve", "ed_restrict", "ed_apply_sz", "ed_lanczos_tridiag", "ed_hamiltonian_store",
+                  "ed_hamiltonian_store_info"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -375,6 +380,27 @@ class Hamiltonian:
     def set_blocks(self, dtype: int, nvec: int, blocks: int):
         """ed_apply_set_blocks: resident blocks per SM for (dtype, nvec class); 0 = default."""
         check(lib().ed_apply_set_blocks(self.handle, dtype, nvec, blocks))
+
+    def store(self, dtype=None, seg_log2: int = 0, max_bytes: int | None = None, stream=None) -> int:
+        """ed_hamiltonian_store: keep H's structure on the device for later applies
+        (segments sized for `dtype`, default the Hamiltonian's FP64 kind); returns
+        its size in bytes.  max_bytes defaults to no limit."""
+        if dtype is None:
+            dtype = ED_F64 if self.is_real else ED_C128
+        nb = ctypes.c_size_t()
+        lim = (1 << 63) if max_bytes is None else int(max_bytes)
+        check(lib().ed_hamiltonian_store(self.handle, int(dtype), int(seg_log2), lim, _stream_handle(stream),
+                                         ctypes.byref(nb)))
+        return int(nb.value)
+
+    def store_info(self) -> dict:
+        e, s, c, b = c_i64(), c_i32(), c_i32(), ctypes.c_size_t()
+        check(lib().ed_hamiltonian_store_info(self.handle, ctypes.byref(e), ctypes.byref(s), ctypes.byref(c),
+                                              ctypes.byref(b)))
+        return dict(entries=int(e.value), segments=int(s.value), codes=int(c.value), bytes=int(b.value))
+
+    def store_free(self):
+        lib().ed_hamiltonian_store_free(self.handle)
 
     def counters(self, stream=None):
         g = c_i64()
