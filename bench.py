@@ -1,12 +1,18 @@
 #!/usr/bin/env python
 """Benchmark of the matrix-free H.x hot path (and Lanczos time-to-E0).
 
-Default workload: the 32-site tilted square cluster (a1=(4,4), a2=(4,-4)),
-J1=1, J2=0.5, Sz=0, symmetry group T32 x C4v (256 elements), sector Gamma.A1,
-FP64 vectors.  One "step" is one y = H x through the C ABI (ed_apply) on a
-seeded synthetic x resident in HBM; L2 is flushed (256 MB write) between
-timed steps.  `e2e` repeats the measurement with x and y in pinned host memory
-(host->device copy, ed_apply, device->host copy inside the timed region).
+Default workload: the 40-site square cluster (a1=(6,2), a2=(-2,6)), J1=1,
+J2=0.55, Sz=0, symmetry group T40 x C4 x Z2 (320 elements), sector
+Gamma.A.even (D = 430,909,650), FP64 vectors -- the largest workload that fits
+one GPU.  One "step" is one y = H x through the C ABI (ed_apply) on a seeded
+synthetic x resident in HBM, on H's stored structure (ed_hamiltonian_store,
+built once per Hamiltonian before the timed region; its build time is
+reported and added to the time-to-E0); the matrix-free kernel is timed beside
+it.  L2 is flushed (256 MB write) between timed steps.  `e2e` repeats the
+measurement with x and y in pinned host memory (host->device copy, ed_apply,
+device->host copy inside the timed region).  Further objects: the 32-site
+square and 36-site chiral kagome workloads, FP64-vs-mixed Lanczos
+time-to-E0, batched sectors, and the CPU oracle's rate.
 
 --impl reference times the CPU oracle (brute-force representatives, FP64) on
 bounded samples of the same workload.
@@ -52,20 +58,20 @@ def peaks():
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("ed_apply.cu", "ed_apply_impl.cuh", "ed_device.cuh", "ed_internal.h"):
+    for f in ("ed_apply.cu", "ed_apply_impl.cuh", "ed_device.cuh", "ed_internal.h", "ed_cache.cu"):
         h.update(open(os.path.join(ROOT, "paper_2210_03511_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str, dtype: str):
-    """DRAM bytes per launch of the H.x kernel and ncu context counters from the
-    committed summary, if it was taken on these kernel sources; else (None, {})."""
+def profiled_traffic(workload: str, dtype: str, kernel: str):
+    """DRAM bytes per H.x of `kernel` and ncu context counters from the committed
+    summary, if it was taken on these kernel sources; else (None, {})."""
     p = os.path.join(ROOT, "profiles", "hx_traffic.txt")
     if not os.path.exists(p):
         return None, {}
     for line in open(p):
         f = line.split()
-        if not f or f[0].startswith("#") or f[0] != f"{workload}:{dtype}":
+        if not f or f[0].startswith("#") or f[0] != f"{workload}:{dtype}:{kernel}":
             continue
         kv = dict(x.split("=", 1) for x in f[1:] if "=" in x)
         if kv.get("kernel_hash") != kernel_hash():
@@ -202,6 +208,128 @@ def oracle_baseline(problem, budget_s: float, cplx: bool, D: int, n_apply=None) 
 
 
 # ------------------------------------------------------------------ main
+KINDS = {"f64": (8, "float64", 0), "f32": (4, "float32", 1), "c128": (16, "complex128", 3), "c64": (8, "complex64", 2)}
+
+
+def _edt(pkg, dtype):
+    return {"f64": pkg.ED_F64, "f32": pkg.ED_F32, "c128": pkg.ED_C128, "c64": pkg.ED_C64}[dtype]
+
+
+def hx_timing(H, edt, x, y, steps, warmup, flush, stream, torch):
+    """Per-launch times (ms) of `steps` ed_apply calls on device-resident x, y (CUDA
+    events on the launching stream, L2 flushed between steps)."""
+    for _ in range(warmup):
+        H.apply_ptr(edt, x.data_ptr(), y.data_ptr(), 1, stream)
+        flush.fill_(1.0)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        H.apply_ptr(edt, x.data_ptr(), y.data_ptr(), 1, stream)
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def stored_bytes(D, G, s_x):
+    """Algorithmic bytes of one stored-structure H.x: per row |Stab| (2), the Ising
+    part (8), x_i and y_i; per element its 4-byte entry and the gathered x_j."""
+    return D * (2 + 8 + 2 * s_x) + G * (4 + s_x)
+
+
+def matrix_free_bytes(D, G, s_x, s_st):
+    """Algorithmic bytes of one matrix-free H.x: per row the state word, |Stab|, x_i
+    and y_i; per gather x_j (lookup tables and Limits reads excluded)."""
+    return D * (s_st + 2 + 2 * s_x) + G * s_x
+
+
+def lanczos_pair(pkg, torch, H, real, D, stream, store_s, n_free_bytes):
+    """Time-to-E0 (1e-10) of the FP64 run and of the mixed run (FP32 vectors, FP64
+    refinement), both on the stored structure built once beforehand (its build
+    time is added to each).  Full reorthogonalisation while 300 stored vectors of
+    the run's dtype fit the memory left beside the structure (FP32 vectors: also
+    100), else the plain recursion."""
+    lz = {}
+    for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
+                             ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
+        s_vec = {pkg.ED_F64: 8, pkg.ED_F32: 4, pkg.ED_C128: 16, pkg.ED_C64: 8}[dt]
+        sizes = (300, 100) if refine else (300,)
+        budget = min(180e9, 0.8 * n_free_bytes)
+        reorth, max_it = next(((True, m) for m in sizes if m * D * s_vec < budget), (False, 300))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=max_it, dtype=dt, reorth=reorth, refine=refine,
+                            raise_on_nonconv=False, stream=stream)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        lz[name] = {"seconds": t + store_s, "lanczos_seconds": t, "store_seconds": store_s, "E0": float(ev[0]),
+                    "iters": rep.iters, "reorth": reorth, "max_iter": max_it, "converged": bool(rep.converged),
+                    "ritz": rep.ritz[0], "n_apply": rep.n_apply}
+    lz["mixed_minus_fp64"] = lz["mixed"]["E0"] - lz["fp64"]["E0"]
+    lz["raw_fp32_minus_fp64"] = lz["mixed"]["ritz"] - lz["fp64"]["E0"]
+    lz["mixed_speedup"] = lz["fp64"]["seconds"] / lz["mixed"]["seconds"]
+    return lz
+
+
+def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3):
+    """Sub-object for a further workload: per dtype the H.x time on the stored
+    structure and matrix-free, their fractions of the HBM roofline, and the
+    FP64-vs-mixed time-to-E0."""
+    from edinputs.vectors import state_vector
+    desc, make = WORKLOADS[name]
+    problem = make()
+    n_terms = len(problem.terms.bonds) + len(problem.terms.tris)
+    real = problem.sector.is_real and problem.terms.is_real
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    basis = pkg.Basis(problem.sector, stream=stream)
+    t_basis = time.perf_counter() - t0
+    H = pkg.Hamiltonian(basis, problem.terms)
+    D = basis.dim
+    reps, _ = basis.export()
+    X = state_vector(7, reps, complex_=not real)
+    peak, _ = peaks()
+    s_st = 4 if problem.sector.n_sites <= 32 else 8
+    out = {"workload": desc, "dim": D, "basis_build_s": round(t_basis, 3)}
+    for dtype in dtypes:
+        s_x, tname, _ = KINDS[dtype]
+        edt = _edt(pkg, dtype)
+        x = torch.tensor(X, device=dev).to(getattr(torch, tname))
+        y = torch.empty_like(x)
+        ms_free = hx_timing(H, edt, x, y, max(2, steps // 2), warmup, flush, stream, torch)
+        G, _ = H.counters(stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.store(edt, stream=stream)
+        torch.cuda.synchronize()
+        t_store = time.perf_counter() - t0
+        info = H.store_info()
+        ms = hx_timing(H, edt, x, y, steps, warmup, flush, stream, torch)
+        t_s, t_f = statistics.mean(ms) / 1e3, statistics.mean(ms_free) / 1e3
+        out[dtype] = {"ms_per_step": t_s * 1e3, "value": D * n_terms / t_s / 1e9, "unit": UNIT,
+                      "frac": stored_bytes(D, G, s_x) / t_s / 1e9 / peak,
+                      "store": {"seconds": round(t_store, 3), "bytes": info["bytes"], "segments": info["segments"],
+                                "codes": info["codes"]},
+                      "matrix_free": {"ms_per_step": t_f * 1e3, "value": D * n_terms / t_f / 1e9,
+                                      "frac": matrix_free_bytes(D, G, s_x, s_st) / t_f / 1e9 / peak}}
+        H.store_free()
+        del x, y
+        torch.cuda.empty_cache()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H.store(_edt(pkg, dtypes[0]), stream=stream)
+    torch.cuda.synchronize()
+    t_store = time.perf_counter() - t0
+    free_b, _ = torch.cuda.mem_get_info()
+    out["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, real, D, stream, t_store, free_b)
+    H.close()
+    basis.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def batching_measurement(pkg, torch, stream):
     """Ground energy of every (k, rho_k) sector of the 24-site triangular torus
     (36 sectors, J1=1, J2=0.125, Sz=0): one Lanczos run per sector in sequence
@@ -252,12 +380,14 @@ def batching_measurement(pkg, torch, stream):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
-    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="square32", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="square40", choices=sorted(WORKLOADS))
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "c128", "c64"])
     ap.add_argument("--no-lanczos", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' sub-objects and batching")
+    ap.add_argument("--matrix-free", action="store_true", help="time the matrix-free kernel only (no stored structure)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     args = ap.parse_args()
@@ -314,118 +444,136 @@ def main():
     H = pkg.Hamiltonian(basis, problem.terms)
     D = basis.dim
     reps, _ = basis.export()
-    tdt = {"f64": torch.float64, "f32": torch.float32, "c128": torch.complex128, "c64": torch.complex64}[dtype]
-    edt = {"f64": pkg.ED_F64, "f32": pkg.ED_F32, "c128": pkg.ED_C128, "c64": pkg.ED_C64}[dtype]
+    s_x, tname, _ = KINDS[dtype]
+    edt = _edt(pkg, dtype)
     X = state_vector(7, reps, complex_=not real)
-    x = torch.tensor(X, device=dev).to(tdt)
+    x = torch.tensor(X, device=dev).to(getattr(torch, tname))
     y = torch.empty_like(x)
+    del X
     flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    for _ in range(args.warmup):
-        H.apply_ptr(edt, x.data_ptr(), y.data_ptr(), 1, stream)
-        flush.fill_(1.0)
-    torch.cuda.synchronize()
+    s_st = 4 if problem.sector.n_sites <= 32 else 8
+    peak, peak_kind = peaks()
+    # the matrix-free kernel first (its gather counter sizes the algorithmic bytes)
+    ms_free = hx_timing(H, edt, x, y, max(3, args.steps // 4), args.warmup, flush, stream, torch)
     gathers, skipped = H.counters(stream)
+    y_free = y.clone() if not args.matrix_free else None
+    store = None
+    if not args.matrix_free:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.store(edt, stream=stream)
+        torch.cuda.synchronize()
+        t_store = time.perf_counter() - t0
+        info = H.store_info()
+        store = {"seconds": round(t_store, 3), "bytes": info["bytes"], "segments": info["segments"],
+                 "codes": info["codes"], "entries": info["entries"]}
     gpu_index = local
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     if cvd and cvd.replace(",", "").isdigit():
         gpu_index = int(cvd.split(",")[local])
     clk = ClockSampler(gpu_index)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clk.start()
     time.sleep(0.3)
     wall0 = time.perf_counter()
-    for i in range(args.steps):
-        flush.fill_(float(i))
-        starts[i].record(stream)
-        H.apply_ptr(edt, x.data_ptr(), y.data_ptr(), 1, stream)
-        ends[i].record(stream)
-    torch.cuda.synchronize()
+    ms = hx_timing(H, edt, x, y, args.steps, args.warmup, flush, stream, torch)
     wall = time.perf_counter() - wall0
     if ws > 1:
         torch.distributed.barrier()
-    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     t_dev = sum(ms) / 1e3
+    stored_diff = None
+    if y_free is not None:
+        # the stored structure gives the matrix-free H x up to the summation order across segments
+        stored_diff = (y - y_free).abs().max().item() / max(y_free.abs().max().item(), 1e-300)
+        del y_free
     # e2e: pinned host x -> device, ed_apply, device -> host, every step
     xh = x.cpu().pin_memory()
     yh = torch.empty_like(xh).pin_memory()
-    xd = torch.empty_like(x)
-    yd = torch.empty_like(x)
     e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for i in range(args.steps):
         flush.fill_(float(i))
         e_s[i].record(stream)
-        xd.copy_(xh, non_blocking=True)
-        H.apply_ptr(edt, xd.data_ptr(), yd.data_ptr(), 1, stream)
-        yh.copy_(yd, non_blocking=True)
+        x.copy_(xh, non_blocking=True)
+        H.apply_ptr(edt, x.data_ptr(), y.data_ptr(), 1, stream)
+        yh.copy_(y, non_blocking=True)
         e_e[i].record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
     t_e2e = sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)) / 1e3
     assert torch.equal(yh, y.cpu()), "e2e result differs from device-resident result"
-    # aggregate over ranks (replicas)
+    h2d, d2h = int(x.numel() * x.element_size()), int(y.numel() * y.element_size())
+    del xh, yh
     t_dev, t_e2e, work = replica_aggregate(t_dev, t_e2e, float(D * n_terms * args.steps), device=dev)
     value = work / t_dev / 1e9
     e2e = work / t_e2e / 1e9
-    # roofline of the H.x kernel: algorithmic bytes per launch
-    s_x = {"f64": 8, "f32": 4, "c128": 16, "c64": 8}[dtype]
-    s_st = 4 if problem.sector.n_sites <= 32 else 8
-    b_alg = D * (s_st + 2 + 2 * s_x) + gathers * s_x
-    per_launch = t_dev / args.steps / ws * ws  # seconds per launch on one GPU
-    achieved = b_alg / (sum(ms) / 1e3 / args.steps) / 1e9
-    peak, peak_kind = peaks()
-    traffic, ncu_ctx = profiled_traffic(args.workload, dtype)
+    t_launch = sum(ms) / 1e3 / args.steps
+    t_free = statistics.mean(ms_free) / 1e3
+    b_free = matrix_free_bytes(D, gathers, s_x, s_st)
+    if args.matrix_free:
+        b_alg, kernel = b_free, "hx_kernel"
+    else:
+        b_alg, kernel = stored_bytes(D, gathers, s_x), "cache_pass_kernel"
+    achieved = b_alg / t_launch / 1e9
+    traffic, ncu_ctx = profiled_traffic(args.workload, dtype, kernel)
+    launches_per_step = 1 if args.matrix_free else store["segments"]
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": desc, "dim": D, "n_terms": n_terms, "n_sym": int(problem.sector.n_sym),
-                       "n_sublat": int(problem.sector.n_sublat), "l2": "flushed: 256 MB write between timed steps",
+                       "n_sublat": int(problem.sector.n_sublat),
+                       "l2": "flushed: 256 MB write between timed steps (inputs also exceed L2)",
+                       "hx_path": "matrix-free" if args.matrix_free else
+                       "stored structure (ed_hamiltonian_store, built once per Hamiltonian, outside the timed region)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "basis_build_s": round(t_basis, 4)},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                       "basis_build_s": round(t_basis, 3)},
+            "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "ncu_context": ncu_ctx,
                          "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": b_alg,
                          "gathers_per_launch": gathers, "incompatible_images_per_launch": skipped,
-                         # the DRAM bytes the launch really moves (ncu, same kernel sources) over the
-                         # same launch time: each gather costs whole random sectors, not s_x bytes
-                         "dram_achieved": (traffic / (sum(ms) / 1e3 / args.steps) / 1e9) if traffic else None,
-                         "dram_frac": (traffic / (sum(ms) / 1e3 / args.steps) / 1e9 / peak) if traffic else None},
-            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": int(x.numel() * x.element_size()),
-                    "d2h_bytes_per_step": int(y.numel() * y.element_size())},
-            "gpu_launches": args.steps,
+                         "launches_per_step": launches_per_step,
+                         "dram_achieved": (traffic / t_launch / 1e9) if traffic else None,
+                         "dram_frac": (traffic / t_launch / 1e9 / peak) if traffic else None},
+            "matrix_free": {"ms_per_step": t_free * 1e3, "value": D * n_terms / t_free / 1e9,
+                            "achieved": b_free / t_free / 1e9, "frac": b_free / t_free / 1e9 / peak},
+            "store": store,
+            "stored_vs_matrix_free_max_rel_diff": stored_diff,
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * launches_per_step,
             "clocks": clocks,
             "wall_s_timed_region": wall}
+    del x, y, flush
+    torch.cuda.empty_cache()
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    # the further measurements must not hide the headline: a failure is recorded, not raised
     if not args.no_lanczos and rank == 0:
-        lz = {}
-        # full reorthogonalisation while the stored vectors of the run's own dtype take
-        # under 180 GB of HBM, else the plain recursion (ghost-filtered, Ritz vectors
-        # from a second pass): FP32 vectors halve that memory, one of the gains of
-        # the mixed-precision run
-        for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
-                                 ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
-            s_vec = {pkg.ED_F64: 8, pkg.ED_F32: 4, pkg.ED_C128: 16, pkg.ED_C64: 8}[dt]
-            # stored vectors are allocated for max_iter steps up front: 300 if they fit;
-            # FP32 vectors (reorthogonalised in FP32 arithmetic, cheap) also 100 (the runs
-            # here converge in under 80 steps); else no storage (FP64 Gram-Schmidt on the
-            # large sectors costs more than the plain recursion saves)
-            sizes = (300, 100) if refine else (300,)
-            reorth, max_it = next(((True, m) for m in sizes if m * D * s_vec < 180e9), (False, 300))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=max_it, dtype=dt, reorth=reorth,
-                                refine=refine, raise_on_nonconv=False, stream=stream)
-            torch.cuda.synchronize()
-            lz[name] = {"seconds": time.perf_counter() - t0, "E0": float(ev[0]), "iters": rep.iters, "reorth": reorth, "max_iter": max_it,
-                        "converged": bool(rep.converged), "ritz": rep.ritz[0], "n_apply": rep.n_apply}
-        lz["mixed_minus_fp64"] = lz["mixed"]["E0"] - lz["fp64"]["E0"]
-        lz["raw_fp32_minus_fp64"] = lz["mixed"]["ritz"] - lz["fp64"]["E0"]
-        line["lanczos_time_to_E0"] = lz
-    if not args.no_lanczos and rank == 0:
-        line["batching_time_to_E0"] = batching_measurement(pkg, torch, stream)
+        if args.matrix_free:
+            t_store = 0.0
+        free_b, _ = torch.cuda.mem_get_info()
+        try:
+            line["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, real, D, stream, t_store, free_b)
+        except Exception as e:
+            line["lanczos_time_to_E0"] = {"error": repr(e)}
+    H.close()
+    basis.close()
+    torch.cuda.empty_cache()
+    if not args.no_extra and rank == 0:
+        extra = {}
+        for name, dts in (("square32", ["f64", "f32"]), ("kagome36", ["c64", "c128"])):
+            if name != args.workload:
+                try:
+                    extra[name] = workload_summary(pkg, torch, name, dts, stream, flush)
+                except Exception as e:
+                    extra[name] = {"error": repr(e)}
+                torch.cuda.empty_cache()
+        line["other_workloads"] = extra
+        if not args.no_lanczos:
+            try:
+                line["batching_time_to_E0"] = batching_measurement(pkg, torch, stream)
+            except Exception as e:
+                line["batching_time_to_E0"] = {"error": repr(e)}
     if rank == 0 and ws == 1 and not args.no_cpu:
         try:
             n_apply = line.get("lanczos_time_to_E0", {}).get("fp64", {}).get("n_apply")

@@ -84,10 +84,15 @@ __global__ void multi_dot(const typename LV<K>::T* A, int64_t ld, const typename
     const int64_t per = (n + gridDim.x - 1) / gridDim.x;
     const int64_t i0 = (int64_t)blockIdx.x * per, i1 = min(n, i0 + per);
     double2 acc = make_double2(0, 0);
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-        const double2 x = ld2(a[i]), y = ld2(b[i]);
-        acc.x += x.x * y.x + x.y * y.y;
-        acc.y += x.x * y.y - x.y * y.x;
+    if constexpr (!LV<K>::cplx) {
+        // real vectors: one FP64 FMA per element (FP64 throughput is scarce on this GPU)
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) acc.x += (double)a[i] * (double)b[i];
+    } else {
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+            const double2 x = ld2(a[i]), y = ld2(b[i]);
+            acc.x += x.x * y.x + x.y * y.y;
+            acc.y += x.x * y.y - x.y * y.x;
+        }
     }
     acc = block_sum2(acc);
     if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = acc;
@@ -176,17 +181,25 @@ __global__ void lanczos_axpy(typename LV<K>::T* w, const typename LV<K>::T* v, c
                              const double2* alpha, const double* beta) {
     const double a = alpha->x;
     const double bt = vp ? *beta : 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 x = ld2(w[i]);
-        const double2 y = ld2(v[i]);
-        x.x -= a * y.x;
-        x.y -= a * y.y;
-        if (vp) {
-            const double2 z = ld2(vp[i]);
-            x.x -= bt * z.x;
-            x.y -= bt * z.y;
+    if constexpr (!LV<K>::cplx) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double x = (double)w[i] - a * (double)v[i];
+            if (vp) x -= bt * (double)vp[i];
+            w[i] = (typename LV<K>::T)x;
         }
-        st2(w[i], x);
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double2 x = ld2(w[i]);
+            const double2 y = ld2(v[i]);
+            x.x -= a * y.x;
+            x.y -= a * y.y;
+            if (vp) {
+                const double2 z = ld2(vp[i]);
+                x.x -= bt * z.x;
+                x.y -= bt * z.y;
+            }
+            st2(w[i], x);
+        }
     }
 }
 
@@ -194,29 +207,45 @@ __global__ void lanczos_axpy(typename LV<K>::T* w, const typename LV<K>::T* v, c
 template <int K>
 __global__ void multi_axpy(typename LV<K>::T* w, const typename LV<K>::T* A, int64_t ld, int nk, const double2* c,
                            int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 x = ld2(w[i]);
-        for (int k = 0; k < nk; ++k) {
-            const double2 a = ld2(A[(int64_t)k * ld + i]);
-            const double2 ck = c[k];
-            x.x -= ck.x * a.x - ck.y * a.y;
-            x.y -= ck.x * a.y + ck.y * a.x;
+    if constexpr (!LV<K>::cplx) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double x = (double)w[i];
+            for (int k = 0; k < nk; ++k) x -= c[k].x * (double)A[(int64_t)k * ld + i];
+            w[i] = (typename LV<K>::T)x;
         }
-        st2(w[i], x);
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double2 x = ld2(w[i]);
+            for (int k = 0; k < nk; ++k) {
+                const double2 a = ld2(A[(int64_t)k * ld + i]);
+                const double2 ck = c[k];
+                x.x -= ck.x * a.x - ck.y * a.y;
+                x.y -= ck.x * a.y + ck.y * a.x;
+            }
+            st2(w[i], x);
+        }
     }
 }
 
 // out = sum_k s_k A_k with real coefficients s (FP64 accumulation, output type O)
 template <int K, typename O>
 __global__ void combine(O* out, const typename LV<K>::T* A, int64_t ld, int nk, const double* s, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 x = make_double2(0, 0);
-        for (int k = 0; k < nk; ++k) {
-            const double2 a = ld2(A[(int64_t)k * ld + i]);
-            x.x += s[k] * a.x;
-            x.y += s[k] * a.y;
+    if constexpr (!LV<K>::cplx) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double x = 0.0;
+            for (int k = 0; k < nk; ++k) x += s[k] * (double)A[(int64_t)k * ld + i];
+            st2(out[i], make_double2(x, 0.0));
         }
-        st2(out[i], x);
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double2 x = make_double2(0, 0);
+            for (int k = 0; k < nk; ++k) {
+                const double2 a = ld2(A[(int64_t)k * ld + i]);
+                x.x += s[k] * a.x;
+                x.y += s[k] * a.y;
+            }
+            st2(out[i], x);
+        }
     }
 }
 
@@ -239,13 +268,23 @@ __global__ void combine_c(typename LV<K>::T* out, const typename LV<K>::T* A, in
 // plain recursion builds Ritz vectors one Lanczos vector at a time
 template <int K, typename O>
 __global__ void accumulate(O* out, int64_t ldo, int nk, const double* c, const typename LV<K>::T* v, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double2 a = ld2(v[i]);
-        for (int k = 0; k < nk; ++k) {
-            double2 x = ld2(out[(int64_t)k * ldo + i]);
-            x.x += c[k] * a.x;
-            x.y += c[k] * a.y;
-            st2(out[(int64_t)k * ldo + i], x);
+    if constexpr (!LV<K>::cplx) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const double a = (double)v[i];
+            for (int k = 0; k < nk; ++k) {
+                const double x = ld2(out[(int64_t)k * ldo + i]).x + c[k] * a;
+                st2(out[(int64_t)k * ldo + i], make_double2(x, 0.0));
+            }
+        }
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            const double2 a = ld2(v[i]);
+            for (int k = 0; k < nk; ++k) {
+                double2 x = ld2(out[(int64_t)k * ldo + i]);
+                x.x += c[k] * a.x;
+                x.y += c[k] * a.y;
+                st2(out[(int64_t)k * ldo + i], x);
+            }
         }
     }
 }
@@ -254,11 +293,16 @@ __global__ void accumulate(O* out, int64_t ldo, int nk, const double* c, const t
 template <int K>
 __global__ void scale_by(typename LV<K>::T* dst, const typename LV<K>::T* src, int64_t n, const double* beta) {
     const double inv = 1.0 / *beta;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        double2 x = ld2(src[i]);
-        x.x *= inv;
-        x.y *= inv;
-        st2(dst[i], x);
+    if constexpr (!LV<K>::cplx) {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+            dst[i] = (typename LV<K>::T)((double)src[i] * inv);
+    } else {
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+            double2 x = ld2(src[i]);
+            x.x *= inv;
+            x.y *= inv;
+            st2(dst[i], x);
+        }
     }
 }
 

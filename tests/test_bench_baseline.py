@@ -19,3 +19,14 @@ def test_oracle_baseline_fields():
     n_terms = len(p.terms.bonds)
     assert 1000 * n_terms / d["hx_seconds_extrapolated"] / 1e9 == pytest.approx(d["value"], rel=1e-9)
     assert "time_to_E0_seconds_extrapolated" not in bench.oracle_baseline(p, 0.1, False, 1000, None)
+
+
+def test_bench_measurement_functions_exist():
+    """Every measurement the default bench line calls is defined (CPU-only import check)."""
+    import bench
+    for name in ("hx_timing", "stored_bytes", "matrix_free_bytes", "lanczos_pair", "workload_summary",
+                 "batching_measurement", "oracle_baseline", "replica_aggregate", "main"):
+        assert callable(getattr(bench, name)), name
+    # algorithmic bytes: per row and per element as documented
+    assert bench.stored_bytes(10, 100, 8) == 10 * (2 + 8 + 16) + 100 * 12
+    assert bench.matrix_free_bytes(10, 100, 4, 8) == 10 * (8 + 2 + 8) + 100 * 4
