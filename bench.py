@@ -248,14 +248,16 @@ def matrix_free_bytes(D, G, s_x, s_st):
 def lanczos_pair(pkg, torch, H, real, D, stream, store_s, n_free_bytes):
     """Time-to-E0 (1e-10) of the FP64 run and of the mixed run (FP32 vectors, FP64
     refinement), both on the stored structure built once beforehand (its build
-    time is added to each).  Full reorthogonalisation while 300 stored vectors of
-    the run's dtype fit the memory left beside the structure (FP32 vectors: also
-    100), else the plain recursion."""
+    time is added to each).  The FP64 run is the thesis's plain three-term
+    recursion (the ground energy needs no stored vectors).  The mixed run needs
+    its Ritz vector for the FP64 Rayleigh quotient: with full
+    reorthogonalisation while 300 (or 100) stored FP32 vectors fit the memory
+    left beside the structure, else the plain recursion and a second pass."""
     lz = {}
     for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
                              ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
         s_vec = {pkg.ED_F64: 8, pkg.ED_F32: 4, pkg.ED_C128: 16, pkg.ED_C64: 8}[dt]
-        sizes = (300, 100) if refine else (300,)
+        sizes = (300, 100) if refine else ()
         budget = min(180e9, 0.8 * n_free_bytes)
         reorth, max_it = next(((True, m) for m in sizes if m * D * s_vec < budget), (False, 300))
         torch.cuda.synchronize()

@@ -308,6 +308,105 @@ __global__ void scale_by(typename LV<K>::T* dst, const typename LV<K>::T* src, i
 
 __global__ void sqrt_re(const double2* in, double* out) { *out = sqrt(in->x); }
 
+// Fused Lanczos step kernels.  Each ends with a grid-wide sum: every block
+// writes its partial, and the block that finishes last (one atomic counter,
+// no waiting) adds all partials in index order with a fixed tree, so the
+// result does not depend on which block was last.  The counter is reset by
+// that block for the next launch.
+__device__ __forceinline__ bool last_block_done(unsigned int* counter) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    return last;
+}
+
+__device__ __forceinline__ double2 sum_partials(const double2* partial, int nb) {
+    double2 acc = make_double2(0, 0);
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+        const double2 v = __ldcg(partial + i);  // L2: written by other blocks of this launch
+        acc.x += v.x;
+        acc.y += v.y;
+    }
+    return block_sum2(acc);  // valid in thread 0
+}
+
+// *out = sum_i conj(a_i) b_i (alpha of a Lanczos step: a = v_n, b = w = H v_n)
+template <int K>
+__global__ void dot_step(const typename LV<K>::T* a, const typename LV<K>::T* b, int64_t n, double2* partial,
+                         unsigned int* counter, double2* out) {
+    double2 acc = make_double2(0, 0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (!LV<K>::cplx) {
+            acc.x += (double)a[i] * (double)b[i];
+        } else {
+            const double2 x = ld2(a[i]), y = ld2(b[i]);
+            acc.x += x.x * y.x + x.y * y.y;
+            acc.y += x.x * y.y - x.y * y.x;
+        }
+    }
+    acc = block_sum2(acc);
+    if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+    if (last_block_done(counter)) {
+        const double2 t = sum_partials(partial, gridDim.x);
+        if (threadIdx.x == 0) {
+            *out = t;
+            *counter = 0u;
+        }
+    }
+}
+
+// w -= alpha v + beta_prev vprev (the arithmetic of lanczos_axpy, so that the
+// second pass of the plain recursion regenerates the vectors bit for bit),
+// then beta_next = |w| of the stored (rounded) w.
+template <int K>
+__global__ void axpy_norm_step(typename LV<K>::T* w, const typename LV<K>::T* v, const typename LV<K>::T* vp,
+                               int64_t n, const double2* alpha, const double* beta_prev, double2* partial,
+                               unsigned int* counter, double* beta_next) {
+    const double a = alpha->x;
+    const double bt = vp ? *beta_prev : 0.0;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (!LV<K>::cplx) {
+            double x = (double)w[i] - a * (double)v[i];
+            if (vp) x -= bt * (double)vp[i];
+            const typename LV<K>::T xr = (typename LV<K>::T)x;
+            w[i] = xr;
+            acc += (double)xr * (double)xr;
+        } else {
+            double2 x = ld2(w[i]);
+            const double2 y = ld2(v[i]);
+            x.x -= a * y.x;
+            x.y -= a * y.y;
+            if (vp) {
+                const double2 z = ld2(vp[i]);
+                x.x -= bt * z.x;
+                x.y -= bt * z.y;
+            }
+            st2(w[i], x);
+            const double2 xr = ld2(w[i]);
+            acc += xr.x * xr.x + xr.y * xr.y;
+        }
+    }
+    const double2 bs = block_sum2(make_double2(acc, 0.0));
+    if (threadIdx.x == 0) partial[blockIdx.x] = bs;
+    if (last_block_done(counter)) {
+        const double2 t = sum_partials(partial, gridDim.x);
+        if (threadIdx.x == 0) {
+            *beta_next = sqrt(t.x);
+            *counter = 0u;
+        }
+    }
+}
+
+// *beta_next = sqrt(sum of the nb partial squared norms) (the reorthogonalised
+// step's |w|, from multi_dot partials)
+__global__ void norm_from_partials(const double2* partial, int nb, double* beta_next) {
+    const double2 t = sum_partials(partial, nb);
+    if (threadIdx.x == 0) *beta_next = sqrt(t.x);
+}
+
 // r = Hy - E y ; FP64 vectors of kind K (0 or 2)
 template <int K>
 __global__ void residual(typename LV<K>::T* r, const typename LV<K>::T* hy, const typename LV<K>::T* y, int64_t n,
@@ -540,11 +639,13 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     const int nstore = o->reorth ? max_it + 1 : 3;
     T* V = (T*)z.get((size_t)nstore * D * sizeof(T));
     T* w = (T*)z.get((size_t)D * sizeof(T));
-    double2* partial = (double2*)z.get((size_t)(max_it + 2) * z.nb * sizeof(double2));
+    // partials: (max_it + 2) vectors' worth for the Gram-Schmidt dots, and two
+    // grids' worth (<= 1024 blocks each) for the fused step kernels
+    const size_t n_part = std::max<size_t>((size_t)(max_it + 2) * z.nb, 2048);
+    double2* partial = (double2*)z.get(n_part * sizeof(double2));
     double2* coef = (double2*)z.get((size_t)(max_it + 2) * sizeof(double2));
     double* beta_d = (double*)z.get(2 * sizeof(double));
-    double2* alpha_d = (double2*)z.get(sizeof(double2));
-    if (!V || !w || !partial || !coef || !beta_d || !alpha_d) return fail(ED_ERR_NOMEM, "Lanczos workspace");
+    if (!V || !w || !partial || !coef || !beta_d) return fail(ED_ERR_NOMEM, "Lanczos workspace");
     const unsigned g = z.grid();
     auto vec = [&](int k) -> T* { return V + (int64_t)(o->reorth ? k : (k % 3)) * D; };
     auto dot = [&](const T* A, int nk, const T* bv, double2* out) {
@@ -578,14 +679,42 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     // Lanczos vectors alone leaves a residual of that size).
     const bool rq_refine = (K == 1 || K == 3) && o->refine > 0;
     std::vector<double> lam_full, rb_full;  // last check: n_eig + 1 Ritz values, residual bounds
-    for (int n = 0; n < max_it; ++n) {
+    // Device history of the recursion: al_dev[n] = (alpha_n, 0), be_dev[n] =
+    // beta_{n+1} = |w_n|; copied to pinned host memory step by step.  The
+    // host reads step n's coefficients only after step n+1 has been queued,
+    // so the GPU never waits for the T-matrix check (one step of look-ahead;
+    // a step queued past convergence is discarded).
+    double2* al_dev = (double2*)z.get((size_t)(max_it + 1) * sizeof(double2));
+    double* be_dev = (double*)z.get((size_t)(max_it + 1) * sizeof(double));
+    unsigned int* ctr = (unsigned int*)z.get(2 * sizeof(unsigned int));
+    if (!al_dev || !be_dev || !ctr) return fail(ED_ERR_NOMEM, "Lanczos workspace");
+    ED_CUDA(cudaMemsetAsync(ctr, 0, 2 * sizeof(unsigned int), s));
+    struct PinnedHist {
+        double* p = nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        ~PinnedHist() {
+            if (p) cudaFreeHost(p);
+            for (auto e : ev)
+                if (e) cudaEventDestroy(e);
+        }
+    } ph;
+    ED_CUDA(cudaHostAlloc((void**)&ph.p, (size_t)(max_it + 1) * 3 * sizeof(double), cudaHostAllocDefault));
+    ED_CUDA(cudaEventCreateWithFlags(&ph.ev[0], cudaEventDisableTiming));
+    ED_CUDA(cudaEventCreateWithFlags(&ph.ev[1], cudaEventDisableTiming));
+    const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((D + 255) / 256, 1024));
+    auto enqueue = [&](int n) -> ed_status {
         ed_status st = apply_launch(h, vdt, vec(n), w, 1, s);
         if (st != ED_OK) return st;
         ++n_apply;
-        dot(vec(n), 1, w, alpha_d);
-        // beta_d still holds beta_n from the previous step
-        lanczos_axpy<K><<<g, 256, 0, s>>>(w, vec(n), n > 0 ? vec(n - 1) : nullptr, D, alpha_d, beta_d);
-        if (o->reorth) {
+        const T* vp = n > 0 ? vec(n - 1) : nullptr;
+        const double* bprev = n > 0 ? be_dev + n - 1 : be_dev;
+        if (!o->reorth) {
+            dot_step<K><<<gs, 256, 0, s>>>(vec(n), w, D, partial, ctr, al_dev + n);
+            axpy_norm_step<K><<<gs, 256, 0, s>>>(w, vec(n), vp, D, al_dev + n, bprev, partial + gs, ctr + 1,
+                                                 be_dev + n);
+        } else {
+            dot_step<K><<<gs, 256, 0, s>>>(vec(n), w, D, partial, ctr, al_dev + n);
+            lanczos_axpy<K><<<g, 256, 0, s>>>(w, vec(n), vp, D, al_dev + n, bprev);
             // classical Gram-Schmidt against all stored vectors, then again
             // against the last two (v_{n-1}, v_n), where the three-term step
             // leaves the largest rounding components
@@ -602,18 +731,35 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
                     multi_axpy<K><<<g, 256, 0, s>>>(w, Vj, D, nj, coef, D);
                 }
             }
+            multi_dot<K><<<dim3(z.nb, 1), 256, 0, s>>>(w, D, w, D, partial);
+            norm_from_partials<<<1, 256, 0, s>>>(partial, z.nb, be_dev + n);
         }
-        dot(w, 1, w, coef + n + 1);
-        sqrt_re<<<1, 1, 0, s>>>(coef + n + 1, beta_d);
-        double2 ah;
-        double bh;
-        ED_CUDA(cudaMemcpyAsync(&ah, alpha_d, sizeof(double2), cudaMemcpyDeviceToHost, s));
-        ED_CUDA(cudaMemcpyAsync(&bh, beta_d, sizeof(double), cudaMemcpyDeviceToHost, s));
-        ED_CUDA(cudaStreamSynchronize(s));
-        al.push_back(ah.x);
+        // v_{n+1} = w / beta_{n+1} (unused when the recursion stops at n)
+        scale_by<K><<<g, 256, 0, s>>>(vec(n + 1), w, D, be_dev + n);
+        ED_CUDA(cudaMemcpyAsync(ph.p + 3 * n, al_dev + n, sizeof(double2), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaMemcpyAsync(ph.p + 3 * n + 2, be_dev + n, sizeof(double), cudaMemcpyDeviceToHost, s));
+        ED_CUDA(cudaEventRecord(ph.ev[n & 1], s));
+        return ED_OK;
+    };
+    {
+        ed_status st = enqueue(0);
+        if (st != ED_OK) return st;
+    }
+    for (int n = 0; n < max_it; ++n) {
+        // queue step n+1 before waiting for step n (the extra slot of the
+        // reorthogonalised basis: nstore = max_it + 1)
+        if (n + 1 < max_it) {
+            ed_status st = enqueue(n + 1);
+            if (st != ED_OK) return st;
+        }
+        ED_CUDA(cudaEventSynchronize(ph.ev[n & 1]));
+        const double ahx = ph.p[3 * n], bh = ph.p[3 * n + 2];
+        // step n+1's event (same slot) may only be re-recorded after this read:
+        // enqueue(n+2) happens in the next iteration, after it
+        al.push_back(ahx);
         be.push_back(bh);
         iters = n + 1;
-        const double tnorm = fabs(ah.x) + bh + 1e-300;
+        const double tnorm = fabs(ahx) + bh + 1e-300;
         const bool breakdown = bh < 1e-13 * tnorm;
         const bool last = breakdown || n + 1 == max_it;
         if ((n + 1) % every == 0 || last) {
@@ -655,8 +801,10 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
             }
         }
         if (conv || last) break;
-        scale_by<K><<<g, 256, 0, s>>>(vec(n + 1), w, D, beta_d);
     }
+    // drain the queued look-ahead step before the workspace is reused
+    ED_CUDA(cudaStreamSynchronize(s));
+    n_apply = iters;
     ED_CUDA(cudaGetLastError());
     const int nk = (int)lam.size();
     ed_lanczos_report r{};
