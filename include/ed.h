@@ -167,12 +167,14 @@ ed_status ed_representatives(const ed_sector* sector, const uint64_t* states, in
  *   states: DEVICE uint64[n], n_sites-bit states (higher bits must be 0).
  *   rep, g, nstab, compat: DEVICE outputs [n], written in full; as in
  *   ed_representatives.  Inputs and outputs are owned by the caller.
- * Asynchronous on `stream`; the table upload is ordered on the same stream.
- * The first call on a device looks up the array's device address (with that
- * device current); make that first call before any stream capture.  Every
- * call shares the one array, which keeps the last call's table image: calls
- * that overlap on the GPU (e.g. on different streams) race and must be
- * serialised by the caller.  Nothing needs zeroing: each call rewrites every
+ * Asynchronous on `stream`; the table upload is ordered on the same stream
+ * and copies from a host buffer that lives only for the call, so the call
+ * must not be made while `stream` is being captured into a CUDA graph: it
+ * then returns ED_ERR_ARG before touching the device.  The first call on a
+ * device looks up the array's device address (with that device current);
+ * host threads may make it concurrently.  Every call shares the one array,
+ * which keeps the last call's table image: calls that overlap on the GPU
+ * (e.g. on different streams) race and must be serialised by the caller.  Nothing needs zeroing: each call rewrites every
  * byte of the array that its kernel reads.  Returns ED_ERR_TABLE_TOO_LARGE
  * if the table image exceeds 224 KB, and the validation errors of
  * ed_basis_build. */

@@ -14,6 +14,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "ed_device.cuh"
@@ -633,28 +634,39 @@ static constexpr size_t kStaticTableBytes = 224 * 1024;
 static __device__ __align__(256) uint8_t g_static_tables[kStaticTableBytes];
 
 // Device address of g_static_tables per device, looked up once per device
-// with that device current (the host-side name is only a stand-in).
+// with that device current (the host-side name is only a stand-in).  The
+// cache is atomic: host threads making their first call on one device at the
+// same time look the address up independently and store the same value.
 static uint8_t* static_tables_ptr(int dev, ed_status& st) {
-    static uint8_t* ptrs[256] = {nullptr};
+    static std::atomic<uint8_t*> ptrs[256];
     st = ED_OK;
     if (dev < 0 || dev >= 256) {
         st = fail(ED_ERR_ARG, "device ordinal %d out of range", dev);
         return nullptr;
     }
-    if (!ptrs[dev]) {
+    uint8_t* cur = ptrs[dev].load(std::memory_order_acquire);
+    if (!cur) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_static_tables);
         if (e != cudaSuccess) {
             st = cuda_fail(e, "cudaGetSymbolAddress(g_static_tables)");
             return nullptr;
         }
-        ptrs[dev] = (uint8_t*)p;
+        cur = (uint8_t*)p;
+        ptrs[dev].store(cur, std::memory_order_release);
     }
-    return ptrs[dev];
+    return cur;
 }
 
 ed_status representatives_static(const ed_sector* sector, const uint64_t* states, int64_t n, uint64_t* rep, int32_t* g,
                                  int32_t* nstab, uint8_t* compat, cudaStream_t s) {
+    // First, before any other CUDA call: the table upload below copies from a
+    // host buffer that lives only for this call, which a captured graph would
+    // read again on every replay, so stream capture is refused.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    ED_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(ED_ERR_ARG, "ed_representatives_noalloc must not be called while its stream is being captured");
     if (!sector || n < 0 || (n > 0 && (!states || !rep || !g || !nstab || !compat)))
         return fail(ED_ERR_ARG, "null argument");
     ed_basis tmp;
