@@ -90,6 +90,7 @@ HxArgs make_args(const ed_hamiltonian* h) {
 
 
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s) {
+    if (L.stored) return cache_batch_launch(L, s);
     switch (L.dtype) {
         case ED_F64: return apply_batch_kind<0>(L, s);
         case ED_F32: return apply_batch_kind<1>(L, s);

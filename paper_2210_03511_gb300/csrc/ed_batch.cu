@@ -16,6 +16,7 @@
 // blocks A_k, B_k and solves the banded T-matrix for eigenvalues by bisection
 // on Sturm (inertia) counts of its banded LDL^H factorisation.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 #include <chrono>
@@ -39,6 +40,11 @@ struct ed_batch {
     std::vector<int64_t> tiles;            // row tiles: (sector, begin, end) triples
     int n_tiles = 0;
     const ed::Alloc* alloc = nullptr;
+    // descriptors of the sectors' stored structures, when every sector has
+    // one (one column segment each): H.x of the batch then streams them
+    mutable std::vector<ed::CacheSector> stored_h;
+    mutable ed::DevBuf d_stored;
+    mutable int64_t stored_slices = 0;
 };
 
 namespace ed {
@@ -447,6 +453,39 @@ static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n)
 
 static int dkind(ed_dtype d) { return d == ED_F64 ? 0 : d == ED_F32 ? 1 : d == ED_C128 ? 2 : 3; }
 
+// The stored-structure descriptors of the batch's sectors (uploaded when
+// they change), or null when some sector has no one-segment structure.
+static const CacheSector* stored_descs(const ed_batch* B, ed_status& st) {
+    st = ED_OK;
+    std::vector<CacheSector> d(B->n);
+    int64_t slices = 0;
+    for (int s = 0; s < B->n; ++s) {
+        if (!cache_sector_desc(B->hs[s], d[s])) return nullptr;
+        d[s].slice0 = slices;
+        slices += d[s].ns;
+    }
+    const bool same = B->stored_h.size() == d.size() &&
+                      memcmp(B->stored_h.data(), d.data(), d.size() * sizeof(CacheSector)) == 0;
+    if (!same) {
+        if (!B->d_stored.p) {
+            B->d_stored.bytes = d.size() * sizeof(CacheSector);
+            B->d_stored.p = B->alloc->get(B->d_stored.bytes, 0);
+            if (!B->d_stored.p) {
+                st = fail(ED_ERR_NOMEM, "batch descriptors");
+                return nullptr;
+            }
+        }
+        if (cudaMemcpy(B->d_stored.p, d.data(), d.size() * sizeof(CacheSector), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+            st = fail(ED_ERR_CUDA, "descriptor upload");
+            return nullptr;
+        }
+        B->stored_h = d;
+        B->stored_slices = slices;
+    }
+    return (const CacheSector*)B->d_stored.p;
+}
+
 static BatchLaunch make_launch(const ed_batch* B, ed_dtype dt, const void* x, void* y, int nvec) {
     BatchLaunch L{};
     L.desc = (const HxArgs*)B->d_desc.p;
@@ -465,6 +504,9 @@ static BatchLaunch make_launch(const ed_batch* B, ed_dtype dt, const void* x, vo
     L.y = y;
     L.counters = (unsigned long long*)B->d_counters.p;
     L.waves = B->waves[dkind(dt)][nvec > 1 ? 1 : 0];
+    ed_status st;
+    L.stored = stored_descs(B, st);
+    L.stored_slices = B->stored_slices;
     return L;
 }
 
@@ -543,6 +585,7 @@ void ed_batch_free(ed_batch* B) {
         B->alloc->put(B->d_row_off.p, B->d_row_off.bytes, 0);
         B->alloc->put(B->d_tiles.p, B->d_tiles.bytes, 0);
         B->alloc->put(B->d_counters.p, B->d_counters.bytes, 0);
+        B->alloc->put(B->d_stored.p, B->d_stored.bytes, 0);
     }
     delete B;
 }

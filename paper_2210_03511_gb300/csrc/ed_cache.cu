@@ -386,6 +386,91 @@ __global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2) cache_pass_kernel(Cach
     }
 }
 
+// All sectors of a batch from their stored structures (one segment each),
+// in one launch: warp w takes slice w of the concatenated slice list, finds
+// its sector from the slices' first indices, and processes it as the mode-0
+// pass of cache_pass_kernel (same sums, same order).  Vectors are those of a
+// batch: sector s's nvec columns start at element nvec * row_off[s].  x may
+// advance by x_step_elems per device-side step (block Lanczos graphs);
+// sectors with active[s] == 0 are skipped.
+template <int K, int NV>
+__global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2)
+    cache_batch_kernel(const CacheSector* __restrict__ sec, int n_sec, int64_t n_slices,
+                       const int64_t* __restrict__ row_off, const void* xv, void* yv, int nvec,
+                       const int* __restrict__ x_step, int64_t x_step_elems, const int* __restrict__ active) {
+    using V = Val<K>;
+    using T = typename V::T;
+    using R = typename V::R;
+    using CT = typename std::conditional<V::cplx, T, R>::type;
+    const T* __restrict__ xb = (const T*)xv;
+    if (x_step) xb += (int64_t)(*x_step) * x_step_elems;
+    T* __restrict__ yb = (T*)yv;
+    const int lane = threadIdx.x & 31;
+    const int nv = NV == 1 ? 1 : nvec;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t gs = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); gs < n_slices; gs += warps) {
+        int lo = 0, hi = n_sec - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sec[mid].slice0 <= gs) lo = mid;
+            else hi = mid - 1;
+        }
+        if (active && !active[lo]) continue;  // uniform over the warp
+        const CacheSector& c = sec[lo];
+        const int64_t ls = gs - c.slice0, row = ls * 32 + lane, D = c.D;
+        const T* __restrict__ x = xb + (int64_t)nv * row_off[lo];
+        T* __restrict__ y = yb + (int64_t)nv * row_off[lo];
+        const CT* __restrict__ ctab;
+        const R* __restrict__ isq;
+        if constexpr (K == 0) ctab = (const CT*)(c.ctab + NCODE * 16);
+        else if constexpr (K == 1) ctab = (const CT*)(c.ctab + NCODE * 32);
+        else if constexpr (K == 2) ctab = (const CT*)c.ctab;
+        else ctab = (const CT*)(c.ctab + NCODE * 24);
+        if constexpr (K == 0 || K == 2) isq = (const R*)c.sq + c.G1;
+        else isq = (const R*)c.sqf + c.G1;
+        const uint32_t ob = c.off_bits, om = (1u << ob) - 1u;
+        const uint32_t my = __ldg(c.counts + row);
+        const uint32_t st = warp_excl_scan(my, lane);
+        const uint32_t* __restrict__ pe = c.ent + __ldg(c.boff + ls) + st;
+        R accr[NV], acci[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) { accr[v] = 0; acci[v] = 0; }
+        for (uint32_t k = 0; k < my; ++k) {
+            const uint32_t w = __ldg(pe + k);
+            const int64_t j = (int64_t)(w & om);
+            const CT cf = __ldg(ctab + (w >> ob));
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+                if (v < nv) {
+                    if constexpr (!V::cplx) {
+                        accr[v] += cf * x[(int64_t)v * D + j];
+                    } else {
+                        const T xj = x[(int64_t)v * D + j];
+                        accr[v] += cf.x * xj.x - cf.y * xj.y;
+                        acci[v] += cf.x * xj.y + cf.y * xj.x;
+                    }
+                }
+        }
+        if (row >= D) continue;
+        const R inv = isq[__ldg(c.stab + row)];
+        const R dg = (R)__ldg(c.diag + row);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v >= nv) continue;
+            const int64_t o = (int64_t)v * D + row;
+            if constexpr (!V::cplx) {
+                y[o] = accr[v] * inv + dg * x[o];
+            } else {
+                const T xi = x[o];
+                T out;
+                out.x = accr[v] * inv + dg * xi.x;
+                out.y = acci[v] * inv + dg * xi.y;
+                y[o] = out;
+            }
+        }
+    }
+}
+
 template <typename W, bool CH, int NS, int PASS>
 static ed_status launch_build(const CacheBuild& c, size_t smem, cudaStream_t s) {
     auto k = cache_build_kernel<W, CH, NS, PASS>;
@@ -445,6 +530,52 @@ struct BuildScratch {
 };
 
 }  // namespace
+
+bool cache_sector_desc(const ed_hamiltonian* h, CacheSector& d) {
+    const HCache& c = h->cache;
+    if (!c.valid || c.nb != 1) return false;
+    const ed_basis* b = h->basis;
+    d.counts = (const uint8_t*)c.counts.p;
+    d.boff = (const uint32_t*)c.boff.p;
+    d.ent = (const uint32_t*)c.ent.p;
+    d.diag = (const double*)c.diag.p;
+    d.stab = (const uint16_t*)b->stab.p;
+    d.ctab = (const uint8_t*)c.ctab.p;
+    d.sq = b->dt.blob + b->dt.off_sqrt;
+    d.sqf = b->dt.blob + b->dt.off_sqrtf;
+    d.D = b->dim;
+    d.ns = c.ns;
+    d.slice0 = 0;
+    d.G1 = b->ht.G + 1;
+    d.off_bits = (uint32_t)c.off_bits;
+    return true;
+}
+
+ed_status cache_batch_launch(const BatchLaunch& L, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    ED_CUDA(cudaGetDevice(&dev));
+    ED_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t blocks_needed = (L.stored_slices + (BLOCK / 32) - 1) / (BLOCK / 32);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)sms * 8));
+    auto go = [&](auto ktag) -> ed_status {
+        constexpr int K = decltype(ktag)::value;
+        if (L.nvec == 1)
+            cache_batch_kernel<K, 1><<<grid, BLOCK, 0, s>>>(L.stored, L.n_sec, L.stored_slices, L.row_off, L.x, L.y,
+                                                            L.nvec, L.x_step, L.x_step_elems, L.active);
+        else
+            cache_batch_kernel<K, MAXV><<<grid, BLOCK, 0, s>>>(L.stored, L.n_sec, L.stored_slices, L.row_off, L.x,
+                                                               L.y, L.nvec, L.x_step, L.x_step_elems, L.active);
+        ED_CUDA(cudaGetLastError());
+        return ED_OK;
+    };
+    switch (L.dtype) {
+        case ED_F64: return go(std::integral_constant<int, 0>{});
+        case ED_F32: return go(std::integral_constant<int, 1>{});
+        case ED_C128: return go(std::integral_constant<int, 2>{});
+        case ED_C64: return go(std::integral_constant<int, 3>{});
+    }
+    return fail(ED_ERR_ARG, "bad dtype");
+}
 
 void cache_free(ed_hamiltonian* h) {
     HCache& c = h->cache;

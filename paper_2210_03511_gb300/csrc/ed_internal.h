@@ -192,6 +192,21 @@ struct HxArgs {
     unsigned long long* counters;  // [0] gathers, [1] incompatible images, [2] missing representatives
 };
 HxArgs make_args(const ed_hamiltonian* h);
+// One sector's stored structure as the batched stored-structure kernel reads
+// it (one column segment; see csrc/ed_cache.cu).
+struct CacheSector {
+    const uint8_t* counts;     // [32 ns] entries per row
+    const uint32_t* boff;      // [ns] first entry of each slice
+    const uint32_t* ent;       // entries: (code << off_bits) | column
+    const double* diag;        // [D] Ising part
+    const uint16_t* stab;      // [D] |Stab sigma_i|
+    const uint8_t* ctab;       // coefficients: [256] double2, [256] double, [256] float2, [256] float
+    const uint8_t* sq;         // sqrt(k) then 1/sqrt(k), k = 0..G (double)
+    const uint8_t* sqf;        // the same in float
+    int64_t D, ns, slice0;     // rows, slices, first slice of the sector in the batch's slice list
+    int G1;                    // G + 1
+    uint32_t off_bits;
+};
 // One batched H.x launch (all sectors of a batch).
 struct BatchLaunch {
     const HxArgs* desc;        // device [n_sec]
@@ -211,8 +226,14 @@ struct BatchLaunch {
     int waves;                 // grid = SMs x resident blocks x waves
     int blocks;                // resident blocks per SM (staging plan of every sector)
     const int* active;         // device [n_sec]: rows of sectors with 0 are skipped (null: all)
+    const CacheSector* stored; // device [n_sec]: every sector's stored structure, or null (matrix-free)
+    int64_t stored_slices;     // slices of 32 rows over all sectors
 };
 ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s);
+// implemented in ed_cache.cu: the batched stored-structure H.x, and the
+// descriptor of one Hamiltonian's structure (false unless stored in one segment)
+ed_status cache_batch_launch(const BatchLaunch& L, cudaStream_t s);
+bool cache_sector_desc(const ed_hamiltonian* h, CacheSector& d);
 size_t hx_smem_bytes(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec, int blocks);
 int hx_default_blocks(const ed_hamiltonian* h, ed_dtype dt, bool ns_ok, int nvec);
 // implemented in ed_basis.cu

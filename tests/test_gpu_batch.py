@@ -102,3 +102,54 @@ def test_batched_single_vector_lanczos(P, tri12, reorth):
     for s, p in enumerate(tri12):
         e0 = np.linalg.eigvalsh(oracle.csr(p).toarray())[0]
         assert abs(ev[s, 0] - e0) <= 1e-10 * max(1.0, abs(e0)), (s, ev[s, 0], e0)
+
+
+@pytest.mark.parametrize("nvec", [1, 3])
+def test_batched_stored_apply(P, tri12, nvec):
+    """Every sector's structure stored (ed_hamiltonian_store, one segment): the batched
+    H.x runs the stored-structure kernel over all sectors and equals each sector's own
+    stored ed_apply (the same sums in the same order; complex products may be contracted
+    into FMAs differently by the two kernels, so to 1e-13 of max|y|), and the
+    matrix-free batched H.x to the FP64 bound."""
+    import torch
+    bases = [P.Basis(p.sector) for p in tri12]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12)]
+    batch = P.Batch(hs)
+    X = _concat(P, tri12, nvec, 3, True)
+    x = torch.tensor(X, dtype=torch.complex128, device="cuda")
+    y_free = torch.empty_like(x)
+    batch.apply(x, y_free, nvec=nvec)
+    for h in hs:
+        h.store()
+    y = torch.empty_like(x)
+    batch.apply(x, y, nvec=nvec)
+    torch.cuda.synchronize()
+    off = batch.row_off
+    for s, h in enumerate(hs):
+        D = int(off[s + 1] - off[s])
+        xs = x[nvec * int(off[s]):nvec * int(off[s + 1])].reshape(nvec, D).contiguous()
+        ys = torch.empty_like(xs)
+        h.apply(xs, ys)
+        torch.cuda.synchronize()
+        ref = y[nvec * int(off[s]):nvec * int(off[s + 1])]
+        assert (ys.reshape(-1) - ref).abs().max().item() <= 1e-13 * max(1.0, ref.abs().max().item())
+    scale = 64 * np.finfo(np.float64).eps * 16 * 0.3 * 8
+    assert (y - y_free).abs().max().item() <= scale * x.abs().max().item()
+
+
+@pytest.mark.parametrize("block,reorth", [(1, False), (1, True), (4, True)])
+def test_batched_stored_lanczos(P, tri12, block, reorth):
+    """Block Lanczos (CUDA graph) on the stored structures of all sectors: each sector's
+    lowest levels against the oracle's dense spectrum."""
+    bases = [P.Basis(p.sector) for p in tri12]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12)]
+    for h in hs:
+        h.store()
+    batch = P.Batch(hs)
+    n_eig = 1 if block == 1 else 3
+    ev, rep = batch.lanczos(block=block, n_eig=n_eig, tol=1e-12, max_iter=300 if block == 1 else 40, seed=5,
+                            use_graph=True, reorth=reorth)
+    assert rep.converged_sectors == len(tri12)
+    for s, p in enumerate(tri12):
+        ref = np.linalg.eigvalsh(oracle.csr(p).toarray())[:n_eig]
+        assert np.allclose(ev[s, :len(ref)], ref, rtol=0, atol=1e-10 * max(1.0, abs(ref[0]))), (s, ev[s], ref)
