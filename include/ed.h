@@ -338,6 +338,13 @@ typedef struct {
                               Ritz vectors in FP64 get one FP64 H.x and their Rayleigh quotients; if
                               r^2/gap misses tol, at most this many FP64 Lanczos steps from their sum */
     int32_t check_every;   /* T-matrix eigensolve every this many steps (>= 1) */
+    int32_t host_vectors;  /* plain recursion only (reorth = 0): 1 = keep every Lanczos vector in host
+                              (system) memory as it is made, on a second stream, and form the Ritz vectors
+                              (evecs, and the mixed refinement's start) from there instead of by a second
+                              pass of iters H.x.  Needs a device that reads pageable host memory (e.g. over
+                              NVLink-C2C); elsewhere the second pass is used.  Host memory: (iters + 1)
+                              vectors of the dtype, reserved for max_iter + 1 and released on return.
+                              0 = second pass */
 } ed_lanczos_opts;
 
 typedef struct {

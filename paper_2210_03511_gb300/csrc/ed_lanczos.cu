@@ -13,8 +13,11 @@
 #include <math.h>
 #include <string.h>
 
+#include <sys/mman.h>
+
 #include <algorithm>
 #include <chrono>
+#include <thread>
 #include <vector>
 
 #include "ed_internal.h"
@@ -621,6 +624,69 @@ static ed_dtype dtype_of() {
     return K == 0 ? ED_F64 : K == 1 ? ED_F32 : K == 2 ? ED_C128 : ED_C64;
 }
 
+// dst[i] = src[i] for n 4-byte words; dst may be pageable host memory (read
+// by the device over NVLink-C2C), so the copy is asynchronous to the host,
+// unlike cudaMemcpyAsync into pageable memory.
+__global__ void copy_words(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, int64_t n) {
+    // 16-byte moves only when both vectors are 16-byte aligned (a Lanczos vector of an
+    // odd dimension in FP32 starts at 8 bytes past a 16-byte boundary)
+    const bool al16 = ((((uintptr_t)dst) | ((uintptr_t)src)) & 15u) == 0;
+    const int64_t n4 = al16 ? n / 4 : 0;
+    uint4* d4 = (uint4*)dst;
+    const uint4* s4 = (const uint4*)src;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (int64_t)gridDim.x * blockDim.x)
+        d4[i] = s4[i];
+    for (int64_t i = n4 * 4 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// Lanczos vectors of the plain recursion kept in host (system) memory, for
+// devices that read pageable host memory (NVLink-C2C): one reserved virtual
+// range for max_iter + 1 vectors, each vector's pages touched by host threads
+// while the GPU works, then filled by a copy kernel on a second stream.  The Ritz vectors are combined from there by the device.
+struct HostKrylov {
+    void* base = nullptr;
+    size_t reserved = 0, vec_bytes = 0;
+    cudaStream_t copy = nullptr;
+    cudaEvent_t made[4] = {}, copied[4] = {};  // by vector index mod 4
+    ~HostKrylov() {
+        if (copy) {
+            cudaStreamSynchronize(copy);
+            cudaStreamDestroy(copy);
+        }
+        for (int i = 0; i < 4; ++i) {
+            if (made[i]) cudaEventDestroy(made[i]);
+            if (copied[i]) cudaEventDestroy(copied[i]);
+        }
+        if (base) munmap(base, reserved);
+    }
+    uint8_t* vec(int k) const { return (uint8_t*)base + (size_t)k * vec_bytes; }
+    // queue the copy of device vector k (made on stream s) to host slot k
+    cudaError_t save(int k, const void* dev, size_t bytes, cudaStream_t s) {
+        touch(k);
+        cudaError_t e = cudaEventRecord(made[k & 3], s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, made[k & 3], 0);
+        if (e == cudaSuccess) {
+            copy_words<<<512, 256, 0, copy>>>((uint32_t*)vec(k), (const uint32_t*)dev, (int64_t)(bytes / 4));
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(copied[k & 3], copy);
+        return e;
+    }
+    // first-touch the pages of vector k (parallel; the copy engine then writes resident pages)
+    void touch(int k) const {
+        const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        const size_t per = (vec_bytes + nth - 1) / nth;
+        std::vector<std::thread> th;
+        for (int t = 0; t < nth; ++t)
+            th.emplace_back([=]() {
+                const size_t a = (size_t)t * per, b = std::min(vec_bytes, a + per);
+                if (a < b) memset(vec(k) + a, 0, b - a);
+            });
+        for (auto& x : th) x.join();
+    }
+};
+
 template <int K>
 static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
                      ed_lanczos_report* rep, cudaStream_t s, const void* start = nullptr) {
@@ -660,6 +726,28 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
     scale_by<K><<<g, 256, 0, s>>>(vec(0), vec(0), D, beta_d);
     ED_CUDA(cudaGetLastError());
+    // Lanczos vectors in host memory (plain recursion whose Ritz vectors are needed)
+    HostKrylov hk;
+    {
+        const bool need_vectors = !o->reorth && (evecs || ((K == 1 || K == 3) && o->refine > 0));
+        int pageable = 0;
+        if (o->host_vectors && need_vectors)
+            ED_CUDA(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, h->basis->device));
+        if (pageable) {
+            hk.vec_bytes = (((size_t)D * sizeof(T)) + 4095) & ~(size_t)4095;
+            hk.reserved = hk.vec_bytes * (size_t)(max_it + 1);
+            void* p = mmap(nullptr, hk.reserved, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS | MAP_NORESERVE,
+                           -1, 0);
+            if (p == MAP_FAILED) return fail(ED_ERR_NOMEM, "host range for %d Lanczos vectors", max_it + 1);
+            hk.base = p;
+            ED_CUDA(cudaStreamCreateWithFlags(&hk.copy, cudaStreamNonBlocking));
+            for (int i = 0; i < 4; ++i) {
+                ED_CUDA(cudaEventCreateWithFlags(&hk.made[i], cudaEventDisableTiming));
+                ED_CUDA(cudaEventCreateWithFlags(&hk.copied[i], cudaEventDisableTiming));
+            }
+            ED_CUDA(hk.save(0, vec(0), (size_t)D * sizeof(T), s));
+        }
+    }
     std::vector<double> al, be;  // al[n] = alpha_n, be[n] = beta_{n+1}
     std::vector<double> prev(n_eig, 0.0), lam;
     std::vector<std::vector<double>> svec;
@@ -734,8 +822,11 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
             multi_dot<K><<<dim3(z.nb, 1), 256, 0, s>>>(w, D, w, D, partial);
             norm_from_partials<<<1, 256, 0, s>>>(partial, z.nb, be_dev + n);
         }
-        // v_{n+1} = w / beta_{n+1} (unused when the recursion stops at n)
+        // v_{n+1} = w / beta_{n+1} (unused when the recursion stops at n); in
+        // the plain recursion its slot held v_{n-2}, whose host copy must be done
+        if (hk.base && n >= 2) ED_CUDA(cudaStreamWaitEvent(s, hk.copied[(n - 2) & 3], 0));
         scale_by<K><<<g, 256, 0, s>>>(vec(n + 1), w, D, be_dev + n);
+        if (hk.base) ED_CUDA(hk.save(n + 1, vec(n + 1), (size_t)D * sizeof(T), s));
         ED_CUDA(cudaMemcpyAsync(ph.p + 3 * n, al_dev + n, sizeof(double2), cudaMemcpyDeviceToHost, s));
         ED_CUDA(cudaMemcpyAsync(ph.p + 3 * n + 2, be_dev + n, sizeof(double), cudaMemcpyDeviceToHost, s));
         ED_CUDA(cudaEventRecord(ph.ev[n & 1], s));
@@ -835,7 +926,15 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         y64 = (T64*)z.get((size_t)ny * D * sizeof(T64));
         if (!y64) return fail(ED_ERR_NOMEM, "refinement workspace");
     }
-    if (!o->reorth && nk > 0 && (evecs || want_refine)) {
+    const T* Vsrc = V;          // stored Lanczos vectors to combine (reorthogonalised run)
+    int64_t Vld = D;
+    if (hk.base) {              // the plain recursion's vectors kept in host memory
+        ED_CUDA(cudaStreamSynchronize(hk.copy));
+        Vsrc = (const T*)hk.base;
+        Vld = (int64_t)(hk.vec_bytes / sizeof(T));
+    }
+    const bool stored_vectors = o->reorth || hk.base;
+    if (!stored_vectors && nk > 0 && (evecs || want_refine)) {
         const int nacc = evecs ? nk : 0;
         const int ncol = nacc + ny;
         std::vector<double2> alh(iters);
@@ -885,12 +984,21 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         }
         ED_CUDA(cudaStreamSynchronize(s));
     }
-    if (o->reorth && evecs) {
+    if (stored_vectors && evecs) {
         double* sd = (double*)z.get((size_t)iters * sizeof(double));
         if (!sd) return fail(ED_ERR_NOMEM, "Ritz workspace");
         for (int k = 0; k < nk; ++k) {
             ED_CUDA(cudaMemcpyAsync(sd, svec[k].data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
-            combine<K, T><<<g, 256, 0, s>>>((T*)evecs + (int64_t)k * D, V, D, iters, sd, D);
+            combine<K, T><<<g, 256, 0, s>>>((T*)evecs + (int64_t)k * D, Vsrc, Vld, iters, sd, D);
+            ED_CUDA(cudaStreamSynchronize(s));
+        }
+        if (hk.base) {  // without reorthogonalisation the Lanczos vectors are not orthogonal: normalise
+            for (int k = 0; k < nk; ++k) {
+                T* ek = (T*)evecs + (int64_t)k * D;
+                dot(ek, 1, ek, coef);
+                sqrt_re<<<1, 1, 0, s>>>(coef, beta_d);
+                scale_by<K><<<g, 256, 0, s>>>(ek, ek, D, beta_d);
+            }
             ED_CUDA(cudaStreamSynchronize(s));
         }
     }
@@ -905,13 +1013,17 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     if constexpr (K == 1 || K == 3) {
         if (want_refine) {
             double* sd = nullptr;
-            if (o->reorth) {
+            if (stored_vectors) {
                 sd = (double*)z.get((size_t)iters * sizeof(double));
                 if (!sd) return fail(ED_ERR_NOMEM, "refinement workspace");
                 for (int k = 0; k <= nk; ++k) {
+                    if (k == nk && nk == 1) {  // the sum of one Ritz vector is that vector
+                        ED_CUDA(cudaMemcpyAsync(y64 + D, y64, (size_t)D * sizeof(T64), cudaMemcpyDeviceToDevice, s));
+                        break;
+                    }
                     const std::vector<double>& cvec = k < nk ? svec[k] : ssum;
                     ED_CUDA(cudaMemcpyAsync(sd, cvec.data(), (size_t)iters * 8, cudaMemcpyHostToDevice, s));
-                    combine<K, T64><<<g, 256, 0, s>>>(y64 + (int64_t)k * D, V, D, iters, sd, D);
+                    combine<K, T64><<<g, 256, 0, s>>>(y64 + (int64_t)k * D, Vsrc, Vld, iters, sd, D);
                     ED_CUDA(cudaStreamSynchronize(s));
                 }
             }

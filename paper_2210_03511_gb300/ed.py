@@ -53,7 +53,7 @@ class ed_allocator(ctypes.Structure):
 
 class ed_lanczos_opts(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int), ("n_eig", c_i32), ("tol", c_dbl), ("max_iter", c_i32), ("reorth", c_i32),
-                ("seed", c_u64), ("refine", c_i32), ("check_every", c_i32)]
+                ("seed", c_u64), ("refine", c_i32), ("check_every", c_i32), ("host_vectors", c_i32)]
 
 
 class ed_block_lanczos_opts(ctypes.Structure):
@@ -409,11 +409,11 @@ class Hamiltonian:
         return int(g.value), int(s.value)
 
     def lanczos(self, n_eig=1, tol=1e-10, max_iter=300, dtype=None, reorth=True, seed=1, refine=False,
-                check_every=1, evecs=None, stream=None, raise_on_nonconv=True):
+                check_every=1, evecs=None, stream=None, raise_on_nonconv=True, host_vectors=False):
         if dtype is None:
             dtype = ED_F64 if self.is_real else ED_C128
         refine = 40 if refine is True else int(refine)
-        o = ed_lanczos_opts(dtype, n_eig, tol, max_iter, int(reorth), seed, refine, check_every)
+        o = ed_lanczos_opts(dtype, n_eig, tol, max_iter, int(reorth), seed, refine, check_every, int(host_vectors))
         ev = (c_dbl * 8)()
         rep = ed_lanczos_report()
         ptr = None
