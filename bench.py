@@ -307,7 +307,7 @@ def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3
         G, _ = H.counters(stream)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H.store(edt, stream=stream)
+        seg, _ = H.store_autotune(edt, stream=stream)  # segment size chosen by timing
         torch.cuda.synchronize()
         t_store = time.perf_counter() - t0
         info = H.store_info()
@@ -315,8 +315,8 @@ def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3
         t_s, t_f = statistics.mean(ms) / 1e3, statistics.mean(ms_free) / 1e3
         out[dtype] = {"ms_per_step": t_s * 1e3, "value": D * n_terms / t_s / 1e9, "unit": UNIT,
                       "frac": stored_bytes(D, G, s_x) / t_s / 1e9 / peak,
-                      "store": {"seconds": round(t_store, 3), "bytes": info["bytes"], "segments": info["segments"],
-                                "codes": info["codes"]},
+                      "store": {"autotune_seconds": round(t_store, 3), "seg_log2": seg, "bytes": info["bytes"],
+                                "segments": info["segments"], "codes": info["codes"]},
                       "matrix_free": {"ms_per_step": t_f * 1e3, "value": D * n_terms / t_f / 1e9,
                                       "frac": matrix_free_bytes(D, G, s_x, s_st) / t_f / 1e9 / peak}}
         H.store_free()
@@ -324,7 +324,7 @@ def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3
         torch.cuda.empty_cache()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    H.store(_edt(pkg, dtypes[0]), stream=stream)
+    H.store(_edt(pkg, dtypes[0]), seg_log2=out[dtypes[0]]["store"]["seg_log2"], stream=stream)
     torch.cuda.synchronize()
     t_store = time.perf_counter() - t0
     free_b, _ = torch.cuda.mem_get_info()
@@ -400,6 +400,8 @@ def main():
     ap.add_argument("--no-lanczos", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workloads' sub-objects and batching")
     ap.add_argument("--matrix-free", action="store_true", help="time the matrix-free kernel only (no stored structure)")
+    ap.add_argument("--seg-log2", type=int, default=0,
+                    help="log2 column-segment size of the stored structure (0: the library's default)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     args = ap.parse_args()
@@ -473,12 +475,12 @@ def main():
     if not args.matrix_free:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H.store(edt, stream=stream)
+        H.store(edt, seg_log2=args.seg_log2, stream=stream)
         torch.cuda.synchronize()
         t_store = time.perf_counter() - t0
         info = H.store_info()
         store = {"seconds": round(t_store, 3), "bytes": info["bytes"], "segments": info["segments"],
-                 "codes": info["codes"], "entries": info["entries"]}
+                 "codes": info["codes"], "entries": info["entries"], "seg_log2": args.seg_log2 or "default"}
     gpu_index = local
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     if cvd and cvd.replace(",", "").isdigit():

@@ -290,6 +290,18 @@ ed_status ed_apply(const ed_hamiltonian* h, ed_dtype dtype, const void* x, void*
 ed_status ed_hamiltonian_store(ed_hamiltonian* h, ed_dtype dtype, int32_t seg_log2, size_t max_bytes,
                                ed_stream stream, size_t* bytes);
 
+/* ed_hamiltonian_store_autotune -- ed_hamiltonian_store with the column
+ * segment chosen by timing: the structure is built for segments of 64, 128 and
+ * 256 MB of `dtype` elements (within 2^5..2^24 elements and 128 segments), one
+ * ed_apply of each is timed on scratch vectors (2 D elements of `dtype` from
+ * the basis's allocator, released on return), and the fastest is kept (built
+ * again if it was not the last one tried).  Fewer, larger segments save the
+ * per-row work of each pass; smaller ones keep the gathered part of x in L2.
+ * *seg_log2 (if non-NULL) receives the chosen log2 segment size, *bytes the
+ * structure's size.  Errors as ed_hamiltonian_store.  Synchronous. */
+ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype dtype, size_t max_bytes, ed_stream stream,
+                                        int32_t* seg_log2, size_t* bytes);
+
 /* Size of the stored structure: entries (off-diagonal elements), column
  * segments, distinct coefficient codes, device bytes; all 0 when none. */
 ed_status ed_hamiltonian_store_info(const ed_hamiltonian* h, int64_t* entries, int32_t* segments, int32_t* codes,

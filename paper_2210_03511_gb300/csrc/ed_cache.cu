@@ -589,20 +589,22 @@ void cache_free(ed_hamiltonian* h) {
     c = HCache{};
 }
 
+// Default column segment: 128 MB of the vector type, at most 2^24 elements.
+static int default_seg_bits(ed_dtype dtype) {
+    const int sx = dtype == ED_F32 ? 4 : dtype == ED_C128 ? 16 : 8;
+    const uint64_t elems = (uint64_t)(128u << 20) / (uint64_t)sx;
+    int bits = 0;
+    while (((uint64_t)2 << bits) <= elems) ++bits;
+    return std::min(bits, 24);
+}
+
 ed_status cache_build(ed_hamiltonian* h, ed_dtype dtype, int seg_log2, size_t max_bytes, cudaStream_t s) {
     const ed_basis* b = h->basis;
     const HostTables& t = b->ht;
     if (h->cache.valid) cache_free(h);
     if (h->n_flip > 255) return fail(ED_ERR_ARG, "the stored structure needs at most 255 flip terms (%d)", h->n_flip);
     const int64_t D = b->dim;
-    int bits = seg_log2;
-    if (bits == 0) {
-        const int sx = dtype == ED_F32 ? 4 : dtype == ED_C128 ? 16 : 8;
-        const uint64_t elems = (uint64_t)(128u << 20) / (uint64_t)sx;  // 128 MB of the vector type per segment
-        bits = 0;
-        while (((uint64_t)2 << bits) <= elems) ++bits;
-        bits = std::min(bits, 24);
-    }
+    int bits = seg_log2 ? seg_log2 : default_seg_bits(dtype);
     if (bits < 5 || bits > 28) return fail(ED_ERR_ARG, "segment bits %d out of range [5,28]", bits);
     const int nb = (int)(((uint64_t)D + ((uint64_t)1 << bits) - 1) >> bits);
     if (nb > CMAXNB) return fail(ED_ERR_ARG, "%d column segments exceed %d; use larger segments", nb, CMAXNB);
@@ -874,4 +876,75 @@ extern "C" void ed_hamiltonian_store_free(ed_hamiltonian* h) {
     if (!h) return;
     cudaSetDevice(h->basis->device);
     ed::cache_free(h);
+}
+
+// Segment-size autotuner: a segment of x must stay in L2 while its pass
+// gathers from it, but every pass also reads each row's count and updates its
+// partial sum, so fewer, larger segments pay where rows are many (the 40-site
+// square sector prefers 128 MB of FP64) and smaller ones where the gathers
+// dominate (the 36-site kagome sector, complex FP32, prefers 64 MB).
+extern "C" ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype dtype, size_t max_bytes,
+                                                   ed_stream stream, int32_t* seg_log2, size_t* bytes) {
+    using namespace ed;
+    if (!h) return fail(ED_ERR_ARG, "null argument");
+    if ((int)dtype < 0 || (int)dtype > 3) return fail(ED_ERR_ARG, "bad dtype");
+    if ((dtype == ED_F64 || dtype == ED_F32) && !h->is_real)
+        return fail(ED_ERR_ARG, "complex Hamiltonian or characters need a complex dtype");
+    cudaSetDevice(h->basis->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t D = h->basis->dim;
+    const int b0 = default_seg_bits(dtype);
+    std::vector<int> cands;
+    for (int b = b0 - 1; b <= b0 + 1; ++b)
+        if (b >= 5 && b <= 24 && (((uint64_t)D + ((uint64_t)1 << b) - 1) >> b) <= (uint64_t)CMAXNB) cands.push_back(b);
+    if (cands.empty()) cands.push_back(b0);
+    const size_t sx = dtype == ED_F32 ? 4 : dtype == ED_C128 ? 16 : 8;
+    const Alloc& A = h->basis->alloc;
+    BuildScratch sc{&A, s, {}};
+    void* x = sc.get((size_t)D * sx);
+    void* y = sc.get((size_t)D * sx);
+    if (!x || !y) return fail(ED_ERR_NOMEM, "autotune vectors");
+    ED_CUDA(cudaMemsetAsync(x, 0, (size_t)D * sx, s));
+    cudaEvent_t e0, e1;
+    ED_CUDA(cudaEventCreate(&e0));
+    ED_CUDA(cudaEventCreate(&e1));
+    struct EFree {
+        cudaEvent_t a, b;
+        ~EFree() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } ef{e0, e1};
+    float best = 1e30f;
+    int best_b = 0;
+    ed_status last = ED_OK;
+    for (int b : cands) {
+        last = cache_build(h, dtype, b, max_bytes, s);
+        if (last == ED_ERR_NOMEM || last == ED_ERR_TABLE_TOO_LARGE || (last == ED_ERR_ARG && b != b0)) continue;
+        if (last != ED_OK) return last;
+        ed_status st = cache_apply(h, dtype, x, y, 1, s);  // warm-up
+        if (st != ED_OK) return st;
+        ED_CUDA(cudaEventRecord(e0, s));
+        for (int r = 0; r < 2 && st == ED_OK; ++r) st = cache_apply(h, dtype, x, y, 1, s);
+        if (st != ED_OK) return st;
+        ED_CUDA(cudaEventRecord(e1, s));
+        ED_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        ED_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            best_b = b;
+        }
+    }
+    if (!best_b) {
+        if (bytes) *bytes = 0;
+        return last != ED_OK ? last : fail(ED_ERR_NOMEM, "no segment size fits the limit");
+    }
+    if (!h->cache.valid || h->cache.seg_bits != best_b) {
+        const ed_status st = cache_build(h, dtype, best_b, max_bytes, s);
+        if (st != ED_OK) return st;
+    }
+    if (seg_log2) *seg_log2 = best_b;
+    if (bytes) *bytes = h->cache.bytes;
+    return ED_OK;
 }

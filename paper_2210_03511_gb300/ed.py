@@ -98,6 +98,8 @@ def lib():
         L.ed_apply_counters.argtypes = [c_vp, c_vp, P(c_i64), P(c_i64)]
         L.ed_hamiltonian_store.argtypes = [c_vp, ctypes.c_int, c_i32, ctypes.c_size_t, c_vp, P(ctypes.c_size_t)]
         L.ed_hamiltonian_store_info.argtypes = [c_vp, P(c_i64), P(c_i32), P(c_i32), P(ctypes.c_size_t)]
+        L.ed_hamiltonian_store_autotune.argtypes = [c_vp, ctypes.c_int, ctypes.c_size_t, c_vp, P(c_i32),
+                                                    P(ctypes.c_size_t)]
         L.ed_hamiltonian_store_free.argtypes = [c_vp]
         L.ed_hamiltonian_store_free.restype = None
         L.ed_lanczos.argtypes = [c_vp, P(ed_lanczos_opts), P(c_dbl), c_vp, P(ed_lanczos_report), c_vp]
@@ -125,7 +127,7 @@ def lib():
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
                   "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation",
                   "ed_time_evolve", "ed_restrict", "ed_apply_sz", "ed_lanczos_tridiag", "ed_hamiltonian_store",
-                  "ed_hamiltonian_store_info"):
+                  "ed_hamiltonian_store_info", "ed_hamiltonian_store_autotune"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -392,6 +394,17 @@ class Hamiltonian:
         check(lib().ed_hamiltonian_store(self.handle, int(dtype), int(seg_log2), lim, _stream_handle(stream),
                                          ctypes.byref(nb)))
         return int(nb.value)
+
+    def store_autotune(self, dtype=None, max_bytes: int | None = None, stream=None) -> tuple[int, int]:
+        """ed_hamiltonian_store_autotune: (chosen log2 segment size, bytes)."""
+        if dtype is None:
+            dtype = ED_F64 if self.is_real else ED_C128
+        sl = c_i32()
+        nb = ctypes.c_size_t()
+        lim = (1 << 63) if max_bytes is None else int(max_bytes)
+        check(lib().ed_hamiltonian_store_autotune(self.handle, int(dtype), lim, _stream_handle(stream),
+                                                  ctypes.byref(sl), ctypes.byref(nb)))
+        return int(sl.value), int(nb.value)
 
     def store_info(self) -> dict:
         e, s, c, b = c_i64(), c_i32(), c_i32(), ctypes.c_size_t()

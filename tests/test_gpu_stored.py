@@ -203,6 +203,24 @@ def test_stored_limit_refused(P):
     assert e.value.name == "ED_ERR_ARG"
 
 
+def test_stored_autotune(P):
+    """The segment-size autotuner keeps one of its candidates (64, 128 or 256 MB of the
+    vector type, here forced to one segment by the small sector), and the kept structure
+    gives the oracle's H x."""
+    import torch
+    p, reps, stab, H = _oracle("kagome18_A")
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    seg, nbytes = h.store_autotune(P.ED_C64)
+    assert seg in (22, 23, 24) and nbytes == h.store_info()["bytes"] > 0
+    X = state_vector(5, reps, complex_=True)
+    x = torch.tensor(X, dtype=torch.complex128, device="cuda")
+    y = torch.empty_like(x)
+    h.apply(x, y)
+    torch.cuda.synchronize()
+    assert np.all(np.abs(y.cpu().numpy() - H @ X) <= _bound(H, X, EPS64))
+
+
 def test_stored_edge_sectors(P):
     """One-state sectors and a Hamiltonian without off-diagonal terms."""
     import torch
