@@ -10,8 +10,8 @@ import math
 
 import numpy as np
 
-from .lattice import (Cluster, build_problem, chain_lattice, kagome_lattice, square_lattice,
-                      triangular_lattice)
+from .lattice import (Cluster, Problem, SectorSUN, Terms, build_problem, chain_lattice, kagome_lattice,
+                      square_lattice, triangular_lattice)
 
 PI = math.pi
 
@@ -127,3 +127,51 @@ def triangular24_sectors(J2=0.125, max_table_bytes=96 * 1024):
     group inside C2v (36 sectors).  Every sector uses the same site numbering
     (2 blocks of 12 sites)."""
     return all_sectors("triangular", [[5, 1], [4, -4]], 1.0, J2, n_sublat=2, max_table_bytes=max_table_bytes)
+
+
+# ---------------------------------------------------------------------------
+# SU(N) models: H = sum_<ij> J_ij P_ij with P_ij the exchange of the colours
+# of sites i and j (the thesis's SU(N) Heisenberg model, chapter on the SU(N)
+# chiral spin liquid), colours in the d-ary encoding of Eq. numberforspinconfig
+# ---------------------------------------------------------------------------
+def sun(kind: str, P, n_colors: int, counts, J1: float = 1.0, J2: float = 0.0, *, k=(0.0, 0.0), irrep=None,
+        point="full", n_sublat: int, translations=True):
+    """SU(n_colors) exchange model on a chain, square or triangular cluster with
+    periodicity P (for a chain P = [[N, 0], [0, 1]]); `counts` colours of each
+    kind.  The site numbering is sublattice-stable with n_sublat blocks (the
+    library packs a site into ceil(log2 n_colors) bits, and a block must fit 16
+    bits)."""
+    lat = {"chain": chain_lattice, "square": square_lattice, "triangular": triangular_lattice}[kind]()
+    cl = Cluster(lat, P)
+    J = {1: J1}
+    if J2:
+        J[2] = J2
+    if irrep is None:
+        irrep = "A" if (kind == "chain" and point == "none") else "A1"
+    if kind == "chain" and point == "none" and irrep == "A1":
+        irrep = "A"
+    spin = build_problem(f"{kind}{cl.N}_su{n_colors}", cl, J=J, point=point, k=k, irrep=irrep, n_sublat=n_sublat,
+                         translations=translations, max_table_bytes=1 << 30)
+    counts = np.asarray(counts, dtype=np.int32)
+    if len(counts) != n_colors or int(counts.sum()) != cl.N:
+        raise ValueError("counts must give one number per colour, summing to the number of sites")
+    s = spin.sector
+    sec = SectorSUN(cl.N, n_colors, counts, s.perm, s.chi, s.n_sublat, label=spin.name)
+    terms = Terms(spin.terms.bonds, spin.terms.J, np.zeros((0, 3), np.int32), np.zeros(0))
+    return Problem(spin.name, sec, terms, dict(spin.meta, counts=counts.tolist(), n_colors=n_colors))
+
+
+def sun_chain(N: int, n_colors: int, counts, J1=1.0, J2=0.0, *, k: int = 0, reflection=False, n_sublat=2,
+              irrep=None):
+    """SU(n_colors) chain of N sites, periodic, momentum 2 pi k / N (with the reflection
+    when `reflection`, irrep of the little group as named by one_d_irreps)."""
+    return sun("chain", [[N, 0], [0, 1]], n_colors, counts, J1, J2, k=(2 * PI * k / N, 0.0),
+               point="full" if reflection else "none", n_sublat=n_sublat, irrep=irrep)
+
+
+def sun_triangular21():
+    """SU(3) Heisenberg model (J1 = 1) on the 21-site triangular torus a1=(4,1), a2=(-1,5)
+    (21 = 4^2 + 4 + 1: the torus keeps the sixfold axis but, being chiral, no mirror),
+    7 sites of each colour, Gamma, fully symmetric irrep of T21 x C6 (126 elements);
+    three blocks of 7 sites (14 bits each)."""
+    return sun("triangular", [[4, 1], [-1, 5]], 3, [7, 7, 7], 1.0, 0.0, irrep="A", n_sublat=3)

@@ -451,6 +451,33 @@ class Sector:
 
 
 @dataclass
+class SectorSUN:
+    """One symmetry sector of an SU(N) model (the library's ed_sector_sun): sites
+    carry one of n_colors colours, colour c occurs counts[c] times (the SU(N)
+    analogue of a fixed S^z), and the group permutes sites (no colour change)."""
+    n_sites: int
+    n_colors: int
+    counts: np.ndarray     # int32 [n_colors], summing to n_sites
+    perm: np.ndarray       # int32 [G][N]
+    chi: np.ndarray        # complex128 [G]
+    n_sublat: int
+    label: str = ""
+
+    @property
+    def n_sym(self) -> int:
+        return len(self.perm)
+
+    @property
+    def is_real(self) -> bool:
+        return bool(np.all(np.abs(self.chi.imag) < 1e-12))
+
+    @property
+    def bits(self) -> int:
+        """Bits per site of the packed colour string: ceil(log2 n_colors)."""
+        return max(1, int(np.ceil(np.log2(self.n_colors))))
+
+
+@dataclass
 class Terms:
     """Hamiltonian H = sum_b J_b S_i.S_j + sum_t Jchi_t S_i.(S_j x S_k)."""
     bonds: np.ndarray      # int32 [nb][2]

@@ -11,3 +11,4 @@ from .core import (apply, basis, binom, build, chirality_sum, correlation_matrix
                    restrict, rows, sector_dim_formula, set_num_threads, sz_spectrum, sz_states,
                    triangle_expectation, lorentzians)
 from .ops import bond_matrix, chirality_matrix  # noqa: F401
+from . import sun  # noqa: F401  (SU(N) exchange models in the d-ary encoding)
