@@ -122,6 +122,47 @@ typedef struct ed_hamiltonian ed_hamiltonian;  /* opaque; basis + prepared terms
  * Returns ED_ERR_EMPTY_SECTOR (and no basis) for a zero-dimensional sector. */
 ed_status ed_basis_build(const ed_sector* sector, const ed_allocator* alloc, ed_stream stream, ed_basis** out);
 
+/* ---------------------------------------------------------------- SU(N) models
+ * Sites carry one of n_colors colours; a configuration is the d-ary integer
+ * sum_k sigma_k d^(N-k) (Eq. numberforspinconfig with local dimension d).
+ * The library packs it into b = ceil(log2 d) bits per site (site 1 in the
+ * most significant b bits), which keeps the order of the d-ary integers, so
+ * representatives (orbit minima) and the sorted basis are those of the d-ary
+ * encoding; ed_basis_export returns the packed words.  A sector fixes how
+ * many sites carry each colour (the SU(N) analogue of fixed S^z). */
+typedef struct {
+    int32_t n_sites;          /* N >= 2, with N * b <= 64 */
+    int32_t n_colors;         /* d, 2 <= d <= 16 */
+    const int32_t* counts;    /* [n_colors] sites of each colour, summing to N (HOST) */
+    int32_t n_sym;            /* |G| >= 1; element 0 must be the identity */
+    const int32_t* perm;      /* [n_sym][n_sites]: the colour on site i moves to perm[g][i] (HOST) */
+    const double* chi;        /* [n_sym][2] = (Re, Im) of chi(g) (HOST) */
+    int32_t n_sublat;         /* blocks of N / n_sublat sites, every element maps blocks onto blocks;
+                                 a block's bits (sites x b) at most 16 */
+} ed_sector_sun;
+
+/* ed_basis_build_sun -- the basis of an SU(N) sector on the device: every
+ * colouring with the given counts, in increasing order, kept iff it is its
+ * own representative with a non-zero projector (as ed_basis_build, with the
+ * group acting on the b bits of each site together).  Validation errors as
+ * ed_basis_build, ED_ERR_ARG for counts that do not add up to n_sites or more
+ * than 64 bits. */
+ed_status ed_basis_build_sun(const ed_sector_sun* sector, const ed_allocator* alloc, ed_stream stream,
+                             ed_basis** out);
+
+/* ed_hamiltonian_create_sun -- H = sum_b J_b P_(i_b j_b), P_ij the exchange of
+ * the colours of sites i and j (Eq. sunexchangeop; the SU(N) Heisenberg model
+ * of Eq. sunheisenbergringex without the ring term), on an SU(N) basis.  The
+ * terms are `terms->bond`, `terms->J` (no triangles: ED_ERR_ARG).  Checks that
+ * every element maps the bond set onto itself; a pair acts iff its colours
+ * differ (amplitude J, element conj(chi(g_tau)) sqrt(|Stab tau~|/|Stab sigma~|) J)
+ * and contributes J to the diagonal when they agree.  The Hamiltonian is
+ * applied through its stored structure (ed_hamiltonian_store), built here
+ * within max_bytes of device memory (ED_ERR_NOMEM above it); ed_apply,
+ * ed_lanczos and the batch calls then work as for spin models.  Synchronous. */
+ed_status ed_hamiltonian_create_sun(const ed_basis* basis, const ed_terms* terms, size_t max_bytes, ed_stream stream,
+                                    ed_hamiltonian** out);
+
 /* Dimension D of the sector. */
 ed_status ed_basis_dim(const ed_basis* basis, int64_t* dim);
 

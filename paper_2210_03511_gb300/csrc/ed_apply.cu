@@ -103,6 +103,8 @@ ed_status apply_batch_launch(const BatchLaunch& L, cudaStream_t s) {
 ed_status apply_launch(const ed_hamiltonian* h, ed_dtype dt, const void* x, void* y, int nvec, cudaStream_t s,
                        bool use_cache) {
     if (use_cache && h->cache.valid) return cache_apply(h, dt, x, y, nvec, s);
+    if (h->sun)
+        return fail(ED_ERR_ARG, "an SU(N) Hamiltonian is applied through its stored structure, which was released");
     const ed_basis* b = h->basis;
     if (h->n_flip > 256) return fail(ED_ERR_ARG, "more than 256 flip terms are not supported");
     HxArgs a = make_args(h);
@@ -132,6 +134,7 @@ extern "C" ed_status ed_apply_autotune(ed_hamiltonian* h, ed_dtype dtype, const 
     using namespace ed;
     if (!h || !x || !y) return fail(ED_ERR_ARG, "null argument");
     if (nvec < 1 || nvec > MAXV) return fail(ED_ERR_ARG, "nvec out of range [1,8]");
+    if (h->sun) return fail(ED_ERR_ARG, "an SU(N) Hamiltonian has no matrix-free kernel to tune");
     cudaStream_t s = (cudaStream_t)stream;
     int& slot = h->tuned_blocks[kind_of(dtype)][nvec > 1 ? 1 : 0];
     const int top = hx_min_blocks(h->basis->word, nvec == 1 ? 1 : MAXV, kind_of(dtype));

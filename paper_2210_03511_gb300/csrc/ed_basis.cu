@@ -66,7 +66,25 @@ struct EnumArgs {
     const uint64_t* offsets;   // pass 1 input
     void* reps;                // pass 1 output (W)
     uint16_t* stab;            // pass 1 output
+    // SU(N) bases: n_colors colours in col_bits bits per site over col_sites
+    // sites; a candidate is kept only if every site holds a colour < n_colors
+    // and colour c occurs col_want[c] times (0 sites: spin-1/2, no filter)
+    int col_sites, col_bits, n_colors;
+    uint64_t col_want[2];      // counts of colours 0..7 and 8..15, one byte each
 };
+
+// Every site's colour below n_colors and the colour counts as wanted.
+template <typename W>
+__device__ __forceinline__ bool colours_ok(W s, const EnumArgs& a) {
+    const W mask = ((W)1 << a.col_bits) - 1;
+    uint64_t got[2] = {0ull, 0ull};
+    for (int k = 0; k < a.col_sites; ++k) {
+        const uint32_t c = (uint32_t)((s >> (k * a.col_bits)) & mask);
+        if (c >= (uint32_t)a.n_colors) return false;
+        got[c >> 3] += 1ull << (8 * (c & 7));
+    }
+    return got[0] == a.col_want[0] && got[1] == a.col_want[1];
+}
 
 template <typename W, bool CHK, int PASS>
 __global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
@@ -92,7 +110,7 @@ __global__ void __launch_bounds__(256) enum_kernel(EnumArgs a) {
             const W s = top | suf;
             int ns;
             bool cp;
-            if (is_rep<W, CHK>(s, t, ns, cp) && cp) {
+            if ((a.col_sites == 0 || colours_ok<W>(s, a)) && is_rep<W, CHK>(s, t, ns, cp) && cp) {
                 if (PASS) {
                     ((W*)a.reps)[out] = s;
                     a.stab[out] = (uint16_t)ns;
@@ -848,6 +866,12 @@ ed_status basis_build_device(ed_basis* b, cudaStream_t s) {
     ED_CUDA(cudaMemcpyAsync(d_segs, segs.data(), segs.size() * sizeof(Seg), cudaMemcpyHostToDevice, s));
     EnumArgs a{};
     a.dt = b->dt;
+    if (b->sun_d) {
+        a.col_sites = b->sun_N;
+        a.col_bits = b->sun_b;
+        a.n_colors = b->sun_d;
+        for (int c = 0; c < b->sun_d; ++c) a.col_want[c >> 3] += (uint64_t)b->sun_counts[c] << (8 * (c & 7));
+    }
     a.segs = d_segs;
     a.n_segs = (int)segs.size();
     a.n_chunks = chunks;

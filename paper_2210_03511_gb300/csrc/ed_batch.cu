@@ -35,6 +35,7 @@ struct ed_batch {
     size_t smem[4][2] = {};   // per dtype, for one / several vectors
     int blocks[4][2] = {};    // resident blocks per SM, same index
     bool w8 = false, chunked = false, ns_ok = false, all_real = true;
+    bool has_sun = false;                  // SU(N) sectors: applied through stored structures only
     int n_sub = 0;
     int waves[4][2] = {{1, 1}, {1, 1}, {1, 1}, {1, 1}};  // [dtype][nvec>1]: tuned grid waves
     std::vector<int64_t> tiles;            // row tiles: (sector, begin, end) triples
@@ -413,6 +414,7 @@ static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n)
         if (h->n_flip > 256) return fail(ED_ERR_ARG, "more than 256 flip terms");
         B->ns_ok = B->ns_ok && b->dt.dl_stride == 4;
         B->all_real = B->all_real && h->is_real;
+        B->has_sun = B->has_sun || h->sun;
         desc[s] = make_args(h);
         B->row_off[s + 1] = B->row_off[s] + b->dim;
     }
@@ -541,6 +543,7 @@ ed_status ed_apply_batch(const ed_batch* B, ed_dtype dtype, const void* x, void*
     if ((dtype == ED_F64 || dtype == ED_F32) && !B->all_real)
         return fail(ED_ERR_ARG, "a complex sector needs a complex dtype");
     BatchLaunch L = make_launch(B, dtype, x, y, nvec);
+    if (B->has_sun && !L.stored) return fail(ED_ERR_ARG, "a batch with SU(N) sectors needs every sector's stored structure");
     ED_CUDA(cudaMemsetAsync(B->d_counters.p, 0, 24, (cudaStream_t)stream));
     return apply_batch_launch(L, (cudaStream_t)stream);
 }
@@ -675,6 +678,7 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     ED_CUDA(cudaGetLastError());
     // one step, all sectors
     BatchLaunch L = make_launch(B, o->dtype, V, W, b);
+    if (B->has_sun && !L.stored) return fail(ED_ERR_ARG, "a batch with SU(N) sectors needs every sector's stored structure");
     L.active = active;
     L.x_step = dk;
     L.x_step_elems = bs;

@@ -52,6 +52,8 @@ struct CacheBuild {
     const uint16_t* hmap;          // [n_flip][8] h-value id by the spins at (a, c0, c1)
     const uint16_t* chi_id;        // [G] id of the exact value chi(g)
     uint32_t n_chi, Gp1;           // code key = (h id * n_chi + chi id) * (G+1) + |Stab tau~|
+    uint64_t dmask;                // bits of one site's state: 1 (spin-1/2) or 2^b - 1 (SU(N) colours)
+    double diag_off;               // Ising part per pair class: jhs(1) (diag_off n_pairs - n_acting): 1/2 spin, 1 SU(N)
     uint32_t* seen;                // bit set of keys that occur  (pass 0)
     const uint8_t* code;           // key -> code               (pass 1)
     unsigned long long* counters;  // [0] entries, [1] incompatible images, [2] missing, [3] overflow
@@ -152,8 +154,9 @@ __global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), 1, 0)) cache_b
                     const int tn = min(32, a.n_flip - 32 * w);
                     uint32_t mw = 0u;
                     for (int bb = 0; bb < tn; ++bb) {
+                        // a term acts iff the two sites' states differ (spins, or packed colours)
                         const uint32_t e = pab[32 * w + bb];
-                        mw |= (uint32_t)(((s >> (e & 0xFFu)) ^ (s >> (e >> 8))) & 1) << bb;
+                        mw |= (uint32_t)((((s >> (e & 0xFFu)) ^ (s >> (e >> 8))) & (W)c.dmask) != 0) << bb;
                     }
                     mask[w] = mw;
                 }
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), 1, 0)) cache_b
                             ntot += __popc(cm);
                         }
                     }
-                    diag += jhs[cc * G1 + 1] * (0.5 * (double)ntot - (double)nact);
+                    diag += jhs[cc * G1 + 1] * (c.diag_off * (double)ntot - (double)nact);
                 }
                 c.diag[row] = diag;
             }
@@ -183,7 +186,9 @@ __global__ void __launch_bounds__(BLOCK, hx_min_blocks(sizeof(W), 1, 0)) cache_b
                     const int tt = 32 * w + ctz32(mw);
                     mw &= mw - 1u;
                     const uint32_t e = pab[tt];
-                    const W tau = s ^ (((W)1 << (e & 0xFFu)) | ((W)1 << (e >> 8)));
+                    // exchange the two sites' states: flip both spins, or swap two packed colours
+                    const W dd = ((s >> (e & 0xFFu)) ^ (s >> (e >> 8))) & (W)c.dmask;
+                    const W tau = s ^ ((dd << (e & 0xFFu)) | (dd << (e >> 8)));
                     W rp;
                     int g, nst;
                     bool cp;
@@ -675,6 +680,8 @@ ed_status cache_build(ed_hamiltonian* h, ed_dtype dtype, int seg_log2, size_t ma
     cb.chi_id = d_chi;
     cb.n_chi = (uint32_t)cval.size();
     cb.Gp1 = (uint32_t)(t.G + 1);
+    cb.dmask = h->sun ? (((uint64_t)1 << b->sun_b) - 1) : 1ull;
+    cb.diag_off = h->sun ? 1.0 : 0.5;
     cb.seen = d_seen;
     cb.code = d_code;
     cb.counters = d_cnt;

@@ -393,6 +393,88 @@ static ed_status prepare_terms(const ed_basis* b, const ed_terms* tm, ed_hamilto
     return ED_OK;
 }
 
+// SU(N) exchange model H = sum_b J_b P_(i_b j_b) (Eq. sunexchangeop): each
+// site pair is one non-branching term; P swaps the two sites' colours, so a
+// term acts iff the colours differ, with amplitude J, and contributes J to the
+// diagonal when they agree.  The flip positions are the lowest bits of the two
+// sites' packed colours.
+static ed_status prepare_terms_sun(const ed_basis* b, const ed_terms* tm, ed_hamiltonian* h) {
+    const int N = b->sun_N, bits = b->sun_b, G = b->ht.G;
+    if (tm->n_bonds < 0) return fail(ED_ERR_ARG, "negative term counts");
+    if (tm->n_tri) return fail(ED_ERR_ARG, "the SU(N) exchange model takes pair terms only");
+    if (tm->n_bonds && (!tm->bond || !tm->J)) return fail(ED_ERR_ARG, "bond/J null");
+    std::map<std::vector<int>, double> bonds;
+    for (int q = 0; q < tm->n_bonds; ++q) {
+        int i = tm->bond[2 * q], j = tm->bond[2 * q + 1];
+        if (i < 0 || i >= N || j < 0 || j >= N || i == j) return fail(ED_ERR_ARG, "bad bond %d (%d,%d)", q, i, j);
+        int a, c;
+        canon_bond(i, j, a, c);
+        bonds[{a, c}] += tm->J[q];
+    }
+    for (int g = 0; g < G; ++g) {
+        const int32_t* p = &b->sun_perm[(size_t)g * N];
+        std::map<std::vector<int>, double> b2;
+        for (auto& kv : bonds) {
+            int a, c;
+            canon_bond(p[kv.first[0]], p[kv.first[1]], a, c);
+            b2[{a, c}] += kv.second;
+        }
+        if (!maps_close(bonds, b2)) return fail(ED_ERR_NOT_SYMMETRIC, "element %d does not map the terms onto themselves", g);
+    }
+    h->flips.clear();
+    std::vector<double> vals;
+    h->jcls.clear();
+    for (auto& kv : bonds) {
+        if (kv.second == 0.0) continue;
+        FlipTerm f{};
+        f.pa = (int8_t)((N - 1 - kv.first[0]) * bits);
+        f.pb = (int8_t)((N - 1 - kv.first[1]) * bits);
+        f.pc0 = f.pc1 = -1;
+        f.jhalf = kv.second;  // the amplitude of P_ij
+        int c = -1;
+        for (size_t k = 0; k < vals.size(); ++k)
+            if (vals[k] == kv.second) { c = (int)k; break; }
+        if (c < 0) { c = (int)vals.size(); vals.push_back(kv.second); }
+        if (c > 255) return fail(ED_ERR_ARG, "more than 256 distinct couplings");
+        h->flips.push_back(f);
+        h->jcls.push_back((uint8_t)c);
+    }
+    h->n_flip = (int)h->flips.size();
+    h->n_diag_bonds = 0;
+    h->n_diag_cls = 0;
+    h->diag_pos.clear();
+    h->diag_cls.clear();
+    h->is_real = b->ht.real_chars;
+    h->sun = true;
+    h->n_jc = (int)vals.size();
+    h->jhs.assign((size_t)h->n_jc * (G + 1), 0.0);
+    for (int c = 0; c < h->n_jc; ++c)
+        for (int n = 0; n <= G; ++n) h->jhs[(size_t)c * (G + 1) + n] = vals[c] * sqrt((double)n);
+    return ED_OK;
+}
+
+static ed_status upload_terms(const ed_basis* basis, ed_hamiltonian* h) {
+    const Alloc& A = basis->alloc;
+    auto up = [&](DevBuf& d, const void* src, size_t bytes) -> bool {
+        d.bytes = bytes ? bytes : 16;
+        d.p = A.get(d.bytes, 0);
+        if (!d.p) return false;
+        if (bytes && cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return false;
+        return true;
+    };
+    bool ok = up(h->d_flips, h->flips.data(), h->flips.size() * sizeof(FlipTerm)) &&
+              up(h->d_diag_pos, h->diag_pos.data(), h->diag_pos.size()) &&
+              up(h->d_diag_cls, h->diag_cls.data(), h->diag_cls.size() * sizeof(DiagClass)) &&
+              up(h->d_jhs, h->jhs.data(), h->jhs.size() * sizeof(double)) &&
+              up(h->d_jcls, h->jcls.data(), h->jcls.size());
+    if (ok) {
+        h->d_counters.bytes = 32;
+        h->d_counters.p = A.get(32, 0);
+        ok = h->d_counters.p && cudaMemset(h->d_counters.p, 0, 32) == cudaSuccess;
+    }
+    return ok ? ED_OK : fail(ED_ERR_NOMEM, "device allocation for terms failed");
+}
+
 }  // namespace ed
 
 using namespace ed;
@@ -419,6 +501,82 @@ ed_status ed_basis_build(const ed_sector* sector, const ed_allocator* alloc, ed_
         return st;
     }
     *out = b;
+    return ED_OK;
+}
+
+ed_status ed_basis_build_sun(const ed_sector_sun* sector, const ed_allocator* alloc, ed_stream stream,
+                             ed_basis** out) {
+    if (!out) return fail(ED_ERR_ARG, "out is null");
+    *out = nullptr;
+    if (!sector || !sector->counts || !sector->perm || !sector->chi) return fail(ED_ERR_ARG, "null argument");
+    const int N = sector->n_sites, d = sector->n_colors, G = sector->n_sym;
+    if (d < 2 || d > 16) return fail(ED_ERR_ARG, "n_colors=%d out of range [2,16]", d);
+    int bits = 1;
+    while ((1 << bits) < d) ++bits;
+    if (N < 2 || N * bits > 64) return fail(ED_ERR_ARG, "%d sites of %d bits exceed 64 bits", N, bits);
+    if (G < 1) return fail(ED_ERR_ARG, "n_sym=%d", G);
+    int tot = 0, pop = 0;
+    for (int c = 0; c < d; ++c) {
+        if (sector->counts[c] < 0) return fail(ED_ERR_ARG, "negative count of colour %d", c);
+        tot += sector->counts[c];
+        pop += sector->counts[c] * __builtin_popcount((unsigned)c);
+    }
+    if (tot != N) return fail(ED_ERR_ARG, "colour counts add up to %d, not %d sites", tot, N);
+    for (int64_t q = 0; q < (int64_t)G * N; ++q)
+        if (sector->perm[q] < 0 || sector->perm[q] >= N) return fail(ED_ERR_NOT_GROUP, "perm entry out of range");
+    // the same group acting on bit positions: bit t of site s moves to bit t of site perm[g][s]
+    std::vector<int32_t> bperm((size_t)G * N * bits);
+    for (int g = 0; g < G; ++g)
+        for (int s2 = 0; s2 < N; ++s2)
+            for (int t = 0; t < bits; ++t)
+                bperm[((size_t)g * N + s2) * bits + t] = sector->perm[(size_t)g * N + s2] * bits + t;
+    ed_sector bs{};
+    bs.n_sites = N * bits;
+    bs.n_up = pop;
+    bs.n_sym = G;
+    bs.perm = bperm.data();
+    bs.spinflip = nullptr;
+    bs.chi = sector->chi;
+    bs.n_sublat = sector->n_sublat;
+    ed_basis* b = new ed_basis();
+    if (alloc) {
+        if (!alloc->alloc || !alloc->free) { delete b; return fail(ED_ERR_ARG, "allocator callbacks null"); }
+        b->alloc.a = *alloc;
+        b->alloc.custom = true;
+    }
+    b->sun_d = d;
+    b->sun_b = bits;
+    b->sun_N = N;
+    b->sun_perm.assign(sector->perm, sector->perm + (size_t)G * N);
+    b->sun_counts.assign(sector->counts, sector->counts + d);
+    ed_status st = build_host_tables(&bs, b->ht);
+    if (st == ED_OK) st = basis_build_device(b, (cudaStream_t)stream);
+    if (st != ED_OK) {
+        ed_basis_free(b);
+        return st;
+    }
+    *out = b;
+    return ED_OK;
+}
+
+ed_status ed_hamiltonian_create_sun(const ed_basis* basis, const ed_terms* terms, size_t max_bytes, ed_stream stream,
+                                    ed_hamiltonian** out) {
+    if (!basis || !terms || !out) return fail(ED_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (!basis->sun_d) return fail(ED_ERR_ARG, "not an SU(N) basis (ed_basis_build_sun)");
+    ed_hamiltonian* h = new ed_hamiltonian();
+    h->basis = basis;
+    ed_status st = prepare_terms_sun(basis, terms, h);
+    if (st == ED_OK) {
+        cudaSetDevice(basis->device);
+        st = upload_terms(basis, h);
+    }
+    if (st == ED_OK) st = cache_build(h, h->is_real ? ED_F64 : ED_C128, 0, max_bytes, (cudaStream_t)stream);
+    if (st != ED_OK) {
+        ed_hamiltonian_free(h);
+        return st;
+    }
+    *out = h;
     return ED_OK;
 }
 
@@ -502,11 +660,13 @@ ed_status ed_representatives_noalloc(const ed_sector* sector, const uint64_t* st
 
 ed_status ed_restrict(const ed_basis* from, const ed_basis* to, ed_dtype dtype, const void* x, void* y, int32_t nvec,
                       ed_stream stream) {
+    if (from && to && (from->sun_d || to->sun_d)) return fail(ED_ERR_ARG, "ed_restrict takes spin-1/2 bases");
     return restrict_vectors(from, to, dtype, x, y, nvec, (cudaStream_t)stream);
 }
 
 ed_status ed_apply_sz(const ed_basis* from, const ed_basis* to, const double* c, ed_dtype dtype, const void* x, void* y,
                       int32_t nvec, ed_stream stream) {
+    if (from && to && (from->sun_d || to->sun_d)) return fail(ED_ERR_ARG, "ed_apply_sz takes spin-1/2 bases");
     return sz_transfer(from, to, c, dtype, x, y, nvec, (cudaStream_t)stream);
 }
 
@@ -522,32 +682,16 @@ void ed_basis_free(ed_basis* b) {
 ed_status ed_hamiltonian_create(const ed_basis* basis, const ed_terms* terms, ed_hamiltonian** out) {
     if (!basis || !terms || !out) return fail(ED_ERR_ARG, "null argument");
     *out = nullptr;
+    if (basis->sun_d) return fail(ED_ERR_ARG, "an SU(N) basis takes ed_hamiltonian_create_sun");
     ed_hamiltonian* h = new ed_hamiltonian();
     h->basis = basis;
     ed_status st = prepare_terms(basis, terms, h);
     if (st != ED_OK) { delete h; return st; }
     cudaSetDevice(basis->device);
-    const Alloc& A = basis->alloc;
-    auto up = [&](DevBuf& d, const void* src, size_t bytes) -> bool {
-        d.bytes = bytes ? bytes : 16;
-        d.p = A.get(d.bytes, 0);
-        if (!d.p) return false;
-        if (bytes && cudaMemcpy(d.p, src, bytes, cudaMemcpyHostToDevice) != cudaSuccess) return false;
-        return true;
-    };
-    bool ok = up(h->d_flips, h->flips.data(), h->flips.size() * sizeof(FlipTerm)) &&
-              up(h->d_diag_pos, h->diag_pos.data(), h->diag_pos.size()) &&
-              up(h->d_diag_cls, h->diag_cls.data(), h->diag_cls.size() * sizeof(DiagClass)) &&
-              up(h->d_jhs, h->jhs.data(), h->jhs.size() * sizeof(double)) &&
-              up(h->d_jcls, h->jcls.data(), h->jcls.size());
-    if (ok) {
-        h->d_counters.bytes = 32;
-        h->d_counters.p = A.get(32, 0);
-        ok = h->d_counters.p && cudaMemset(h->d_counters.p, 0, 32) == cudaSuccess;
-    }
-    if (!ok) {
+    st = upload_terms(basis, h);
+    if (st != ED_OK) {
         ed_hamiltonian_free(h);
-        return fail(ED_ERR_NOMEM, "device allocation for terms failed");
+        return st;
     }
     *out = h;
     return ED_OK;

@@ -128,6 +128,13 @@ struct ed_basis {
     ed::DevBuf limits;
     uint64_t n_keys = 0;
     int device = 0;
+    // SU(N) basis (ed_basis_build_sun): colours in sun_b bits per site; the
+    // tables above act on the n_sites * sun_b bit positions
+    int sun_d = 0;                      // number of colours (0: spin-1/2 basis)
+    int sun_b = 1;                      // bits per site
+    int sun_N = 0;                      // sites
+    std::vector<int32_t> sun_perm;      // [G][sun_N] site permutations
+    std::vector<int32_t> sun_counts;    // [sun_d]
     size_t dir_q_off() const { return (size_t)((1 << ht.m) + 1) * 4; }
     size_t dir_lim_off() const { return (dir_q_off() + (size_t)(((1 << ht.m) + 15) & ~15) + 15) & ~(size_t)15; }
 };
@@ -163,6 +170,7 @@ struct ed_hamiltonian {
     std::vector<uint8_t> jcls;          // [n_flip]
     ed::DevBuf d_jhs, d_jcls;
     int tuned_blocks[4][2] = {};        // resident H.x blocks per SM by dtype, nvec == 1 / > 1 (0: default)
+    bool sun = false;                   // SU(N) exchange model: applied through its stored structure only
     ed::HCache cache;                   // stored structure, when built (ed_hamiltonian_store)
 };
 

@@ -38,6 +38,11 @@ class ed_sector(ctypes.Structure):
                 ("chi", P(c_dbl)), ("n_sublat", c_i32)]
 
 
+class ed_sector_sun(ctypes.Structure):
+    _fields_ = [("n_sites", c_i32), ("n_colors", c_i32), ("counts", P(c_i32)), ("n_sym", c_i32),
+                ("perm", P(c_i32)), ("chi", P(c_dbl)), ("n_sublat", c_i32)]
+
+
 class ed_terms(ctypes.Structure):
     _fields_ = [("n_bonds", c_i32), ("bond", P(c_i32)), ("J", P(c_dbl)), ("n_tri", c_i32), ("tri", P(c_i32)),
                 ("Jchi", P(c_dbl))]
@@ -84,6 +89,8 @@ def lib():
         L = ctypes.CDLL(LIB_PATH)
         L.ed_basis_build.argtypes = [P(ed_sector), P(ed_allocator), c_vp, P(c_vp)]
         L.ed_basis_dim.argtypes = [c_vp, P(c_i64)]
+        L.ed_basis_build_sun.argtypes = [P(ed_sector_sun), P(ed_allocator), c_vp, P(c_vp)]
+        L.ed_hamiltonian_create_sun.argtypes = [c_vp, P(ed_terms), ctypes.c_size_t, c_vp, P(c_vp)]
         L.ed_basis_export.argtypes = [c_vp, P(c_u64), P(c_u16)]
         L.ed_sector_tables.argtypes = [P(ed_sector), P(c_u16), P(c_u32), P(c_u16), P(c_i64), P(c_u16), P(c_u8)]
         L.ed_representatives.argtypes = [P(ed_sector), P(c_u64), c_i64, P(c_u64), P(c_i32), P(c_i32), P(c_u8)]
@@ -127,7 +134,8 @@ def lib():
                   "ed_hamiltonian_is_real", "ed_apply", "ed_apply_counters", "ed_apply_autotune",
                   "ed_apply_set_blocks", "ed_lanczos", "ed_tridiag_eigs", "ed_expectation",
                   "ed_time_evolve", "ed_restrict", "ed_apply_sz", "ed_lanczos_tridiag", "ed_hamiltonian_store",
-                  "ed_hamiltonian_store_info", "ed_hamiltonian_store_autotune"):
+                  "ed_hamiltonian_store_info", "ed_hamiltonian_store_autotune", "ed_basis_build_sun",
+                  "ed_hamiltonian_create_sun"):
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
@@ -278,10 +286,32 @@ class Basis:
             pass
 
 
-class Hamiltonian:
-    """ed_hamiltonian_create / ed_apply / ed_lanczos."""
+class BasisSUN(Basis):
+    """ed_basis_build_sun: the basis of an SU(N) sector (colours packed in
+    ceil(log2 n_colors) bits per site; export() returns the packed words)."""
 
-    def __init__(self, basis: Basis, terms):
+    def __init__(self, sector, stream=None):
+        perm = np.ascontiguousarray(sector.perm, dtype=np.int32)
+        counts = np.ascontiguousarray(sector.counts, dtype=np.int32)
+        chi = np.asarray(sector.chi, dtype=complex)
+        chi2 = np.ascontiguousarray(np.stack([chi.real, chi.imag], axis=1), dtype=np.float64)
+        self._sec = ed_sector_sun(int(sector.n_sites), int(sector.n_colors), _ptr(counts, c_i32), int(len(perm)),
+                                  _ptr(perm, c_i32), _ptr(chi2, c_dbl), int(sector.n_sublat))
+        self._keep = [perm, counts, chi2]
+        self.n_sites = int(sector.n_sites)
+        self.n_colors = int(sector.n_colors)
+        self.handle = c_vp()
+        check(lib().ed_basis_build_sun(ctypes.byref(self._sec), None, _stream_handle(stream),
+                                       ctypes.byref(self.handle)))
+        d = c_i64()
+        check(lib().ed_basis_dim(self.handle, ctypes.byref(d)))
+        self.dim = int(d.value)
+
+
+class Hamiltonian:
+    """ed_hamiltonian_create / ed_apply / ed_lanczos (ed_hamiltonian_create_sun for an SU(N) basis)."""
+
+    def __init__(self, basis: Basis, terms, max_bytes: int | None = None, stream=None):
         self.basis = basis
         bonds = np.ascontiguousarray(np.asarray(terms.bonds, dtype=np.int32).reshape(-1, 2))
         J = np.ascontiguousarray(terms.J, dtype=np.float64)
@@ -290,7 +320,12 @@ class Hamiltonian:
         self._keep = [bonds, J, tris, Jc]
         t = ed_terms(len(bonds), _ptr(bonds, c_i32), _ptr(J, c_dbl), len(tris), _ptr(tris, c_i32), _ptr(Jc, c_dbl))
         self.handle = c_vp()
-        check(lib().ed_hamiltonian_create(basis.handle, ctypes.byref(t), ctypes.byref(self.handle)))
+        if isinstance(basis, BasisSUN):
+            lim = (1 << 63) if max_bytes is None else int(max_bytes)
+            check(lib().ed_hamiltonian_create_sun(basis.handle, ctypes.byref(t), lim, _stream_handle(stream),
+                                                  ctypes.byref(self.handle)))
+        else:
+            check(lib().ed_hamiltonian_create(basis.handle, ctypes.byref(t), ctypes.byref(self.handle)))
         r = c_i32()
         check(lib().ed_hamiltonian_is_real(self.handle, ctypes.byref(r)))
         self.is_real = bool(r.value)
