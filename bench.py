@@ -335,6 +335,46 @@ def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3
     return out
 
 
+def sun_summary(pkg, torch, stream, flush, steps=10, warmup=3):
+    """SU(3) exchange model on the 21-site triangular torus (T21 x C6, 7 sites of each
+    colour, d-ary colours packed in 2 bits a site): basis and stored-structure build,
+    H.x (FP64, FP32) and FP64-vs-mixed time-to-E0."""
+    from edinputs import configs as EC
+    from edinputs.vectors import state_vector
+    p = EC.sun_triangular21()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t0 = time.perf_counter()
+    b = pkg.BasisSUN(p.sector, stream=stream)
+    t_basis = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    H = pkg.Hamiltonian(b, p.terms, stream=stream)  # builds the stored structure
+    torch.cuda.synchronize()
+    t_store = time.perf_counter() - t0
+    reps, _ = b.export()
+    X = state_vector(7, reps)
+    n_terms = len(p.terms.bonds)
+    out = {"workload": "SU(3) exchange model, triangular 21 sites (4,1)x(-1,5), T21xC6, Gamma.A, 7 sites per colour",
+           "dim": b.dim, "basis_build_s": round(t_basis, 3), "store_s": round(t_store, 3),
+           "store_bytes": H.store_info()["bytes"]}
+    G = H.store_info()["entries"]
+    peak, _ = peaks()
+    for dtype in ("f64", "f32"):
+        s_x, tname, _ = KINDS[dtype]
+        x = torch.tensor(X, device=dev).to(getattr(torch, tname))
+        y = torch.empty_like(x)
+        ms = hx_timing(H, _edt(pkg, dtype), x, y, steps, warmup, flush, stream, torch)
+        t = statistics.mean(ms) / 1e3
+        out[dtype] = {"ms_per_step": t * 1e3, "value": b.dim * n_terms / t / 1e9, "unit": UNIT,
+                      "frac": stored_bytes(b.dim, G, s_x) / t / 1e9 / peak}
+    free_b, _ = torch.cuda.mem_get_info()
+    out["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, True, b.dim, stream, t_store, free_b)
+    H.close()
+    b.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def batching_measurement(pkg, torch, stream):
     """Ground energy of every (k, rho_k) sector of the 24-site triangular torus
     (36 sectors, J1=1, J2=0.125, Sz=0): one Lanczos run per sector in sequence
@@ -582,6 +622,10 @@ def main():
                 except Exception as e:
                     extra[name] = {"error": repr(e)}
                 torch.cuda.empty_cache()
+        try:
+            extra["su3_triangular21"] = sun_summary(pkg, torch, stream, flush)
+        except Exception as e:
+            extra["su3_triangular21"] = {"error": repr(e)}
         line["other_workloads"] = extra
         if not args.no_lanczos:
             try:

@@ -23,7 +23,8 @@ What it computes, from the thesis:
     dim = (1/|G|) sum_g conj(chi(g)) Fix(g), Fix(g) the colourings with the
     given counts that are constant on every cycle of g -- `sector_dim_formula`;
   * the library's packed form of a colouring (ceil(log2 d) bits per site,
-    site 1 most significant; the same order as the d-ary integers) -- `packed`.
+    site 1 most significant; the same order as the d-ary integers) -- `packed`;
+  * matrix-free rows of H for sampled representatives -- `rows`.
 """
 from __future__ import annotations
 
@@ -244,3 +245,29 @@ def packed(state: int, N: int, d: int) -> int:
     for c in digits(state, N, d):
         v = (v << b) | int(c)
     return v
+
+
+def rows(problem, reps, x_of):
+    """Matrix-free rows for given representatives sigma~ (d-ary integers of compatible
+    representatives): y(sigma~) = sum_j H[sigma~, j] x_j with H[i, j] = conj(H[j, i])
+    (H Hermitian), the column of sigma~ formed as in `csr`, and x_j = x_of(tau~) for the
+    representative tau~ (a d-ary integer) of index j."""
+    sec, terms = problem.sector, problem.terms
+    N, d = int(sec.n_sites), int(sec.n_colors)
+    out = np.zeros(len(reps), dtype=complex)
+    for q, s in enumerate(reps):
+        s = int(s)
+        r0, g0, n0, s0 = rep(sec, s)
+        assert r0 == s and abs(s0) > 1e-9
+        acc = 0j
+        for (i, j), J in zip(terms.bonds, terms.J):
+            t = _swap(s, N, d, int(i), int(j))
+            if t is None:
+                acc += J * x_of(s)
+                continue
+            r, g, n, ssum = rep(sec, t)
+            if abs(ssum) < 1e-9:
+                continue
+            acc += np.conj(J * np.conj(sec.chi[g]) * np.sqrt(n / n0)) * x_of(r)
+        out[q] = acc
+    return out

@@ -24,7 +24,7 @@ def test_oracle_baseline_fields():
 def test_bench_measurement_functions_exist():
     """Every measurement the default bench line calls is defined (CPU-only import check)."""
     import bench
-    for name in ("hx_timing", "stored_bytes", "matrix_free_bytes", "lanczos_pair", "workload_summary",
+    for name in ("hx_timing", "stored_bytes", "matrix_free_bytes", "lanczos_pair", "workload_summary", "sun_summary",
                  "batching_measurement", "oracle_baseline", "replica_aggregate", "main"):
         assert callable(getattr(bench, name)), name
     # algorithmic bytes: per row and per element as documented
