@@ -245,32 +245,26 @@ def matrix_free_bytes(D, G, s_x, s_st):
     return D * (s_st + 2 + 2 * s_x) + G * s_x
 
 
-def lanczos_pair(pkg, torch, H, real, D, stream, store_s, n_free_bytes):
+def lanczos_pair(pkg, torch, H, real, D, stream, store_for):
     """Time-to-E0 (1e-10) of the FP64 run and of the mixed run (FP32 vectors, FP64
-    refinement), both on the stored structure built once beforehand (its build
-    time is added to each).  The FP64 run is the thesis's plain three-term
-    recursion (the ground energy needs no stored vectors).  The mixed run needs
-    its Ritz vector for the FP64 Rayleigh quotient: with full
-    reorthogonalisation while 300 (or 100) stored FP32 vectors fit the memory
-    left beside the structure, else the plain recursion and a second pass."""
+    refinement), each on H's stored structure as store_for(dtype) prepares it
+    (returning the seconds its build took, added to the run's time).  The FP64
+    run is the thesis's plain three-term recursion (the ground energy needs no
+    stored vectors); the mixed run needs its Ritz vector for the FP64 Rayleigh
+    quotient and keeps its Lanczos vectors in host memory (NVLink-C2C) instead of
+    running a second pass."""
     lz = {}
     for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
                              ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
-        s_vec = {pkg.ED_F64: 8, pkg.ED_F32: 4, pkg.ED_C128: 16, pkg.ED_C64: 8}[dt]
-        sizes = (300, 100) if refine else ()
-        budget = min(180e9, 0.8 * n_free_bytes)
-        reorth, max_it = next(((True, m) for m in sizes if m * D * s_vec < budget), (False, 300))
+        store_s = store_for(dt)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        # the mixed run without stored vectors keeps its Lanczos vectors in host memory
-        # (no second pass for the Ritz vector) where the device reads pageable host memory
-        host_v = bool(refine and not reorth)
-        ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=max_it, dtype=dt, reorth=reorth, refine=refine,
-                            raise_on_nonconv=False, stream=stream, host_vectors=host_v)
+        ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=300, dtype=dt, reorth=False, refine=refine,
+                            raise_on_nonconv=False, stream=stream, host_vectors=refine)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         lz[name] = {"seconds": t + store_s, "lanczos_seconds": t, "store_seconds": store_s, "E0": float(ev[0]),
-                    "iters": rep.iters, "reorth": reorth, "host_vectors": host_v, "max_iter": max_it,
+                    "iters": rep.iters, "reorth": False, "host_vectors": refine, "max_iter": 300,
                     "converged": bool(rep.converged), "ritz": rep.ritz[0], "n_apply": rep.n_apply}
     lz["mixed_minus_fp64"] = lz["mixed"]["E0"] - lz["fp64"]["E0"]
     lz["raw_fp32_minus_fp64"] = lz["mixed"]["ritz"] - lz["fp64"]["E0"]
@@ -322,13 +316,16 @@ def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3
         H.store_free()
         del x, y
         torch.cuda.empty_cache()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    H.store(_edt(pkg, dtypes[0]), seg_log2=out[dtypes[0]]["store"]["seg_log2"], stream=stream)
-    torch.cuda.synchronize()
-    t_store = time.perf_counter() - t0
-    free_b, _ = torch.cuda.mem_get_info()
-    out["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, real, D, stream, t_store, free_b)
+    seg_of = {_edt(pkg, dt): out[dt]["store"]["seg_log2"] for dt in dtypes}
+
+    def store_for(edt):  # the structure with the segment size tuned for this dtype
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        H.store(edt, seg_log2=seg_of[edt], stream=stream)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    out["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, real, D, stream, store_for)
     H.close()
     basis.close()
     torch.cuda.empty_cache()
@@ -367,8 +364,7 @@ def sun_summary(pkg, torch, stream, flush, steps=10, warmup=3):
         t = statistics.mean(ms) / 1e3
         out[dtype] = {"ms_per_step": t * 1e3, "value": b.dim * n_terms / t / 1e9, "unit": UNIT,
                       "frac": stored_bytes(b.dim, G, s_x) / t / 1e9 / peak}
-    free_b, _ = torch.cuda.mem_get_info()
-    out["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, True, b.dim, stream, t_store, free_b)
+    out["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, True, b.dim, stream, lambda edt: t_store)
     H.close()
     b.close()
     torch.cuda.empty_cache()
@@ -605,9 +601,9 @@ def main():
     if not args.no_lanczos and rank == 0:
         if args.matrix_free:
             t_store = 0.0
-        free_b, _ = torch.cuda.mem_get_info()
         try:
-            line["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, real, D, stream, t_store, free_b)
+            # one structure serves both runs (FP64 and FP32 segments are the same size here)
+            line["lanczos_time_to_E0"] = lanczos_pair(pkg, torch, H, real, D, stream, lambda edt: t_store)
         except Exception as e:
             line["lanczos_time_to_E0"] = {"error": repr(e)}
     H.close()
