@@ -73,6 +73,7 @@ struct CachePass {
     int64_t D, ns, xoff;     // xoff: first column of the segment
     int nvec, mode;
     uint32_t off_bits;       // entry = (code << off_bits) | column offset
+    uint32_t n_re;           // codes below n_re have real coefficients (complex kinds)
 };
 
 __device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane) {
@@ -274,6 +275,10 @@ __global__ void slice_offsets(const uint64_t* abs_off, int64_t ns, int nb, uint3
     }
 }
 
+// Resident blocks per SM of a pass launch: 32 registers a thread for one
+// vector (complex FP64 takes 40 to keep its accumulators out of local memory).
+constexpr int pass_blocks(int K, int NV) { return NV == 1 ? (K == 2 ? 6 : 8) : 2; }
+
 // One segment's pass of y = H x from the stored structure: one warp per
 // slice of 32 rows, one lane per row.  With tens of segments a row has only a
 // few entries per segment, so a pass is bound by the latency of each slice's
@@ -281,11 +286,20 @@ __global__ void slice_offsets(const uint64_t* abs_off, int64_t ns, int nb, uint3
 // the next slice's count and offset, and this row's partial sum of earlier
 // segments, before it walks the current entries, two at a time.  (Walking
 // several slices side by side cost registers and occupancy and was slower.)
-// In mode 0 every row sums its entries in the matrix-free kernel's order
-// with the same coefficients, so for real vector types the result is
-// bit-identical to it.
-template <int K, int NV>
-__global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2) cache_pass_kernel(CachePass p) {
+// A row's sum continues from that partial sum (no separate add per row and
+// segment: FP64 arithmetic is scarce on this GPU).  In mode 0 every row sums
+// its entries in the matrix-free kernel's order with the same coefficients,
+// so for real vector types the result is bit-identical to it.
+// AX (complex kinds): every code's coefficient is real or purely imaginary
+// (real characters: Heisenberg terms real, chirality terms imaginary), so one
+// entry costs two real multiply-adds instead of four.  The real codes come
+// first (codes below p.n_re), so the choice is an integer compare; the table
+// holds (c, c) for a real c and (-c, c) for i c, and the imaginary case takes
+// x_j's parts swapped.
+// PREV: modes 2 and 3 (a partial sum from earlier segments exists), a
+// compile-time flag so that the one-segment pass carries no such register.
+template <int K, int NV, bool AX, bool PREV>
+__global__ void __launch_bounds__(BLOCK, pass_blocks(K, NV)) cache_pass_kernel(CachePass p) {
     using V = Val<K>;
     using T = typename V::T;
     using R = typename V::R;
@@ -299,7 +313,7 @@ __global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2) cache_pass_kernel(Cach
     const int lane = threadIdx.x & 31;
     const int nvec = NV == 1 ? 1 : p.nvec;
     const int64_t D = p.D;
-    const uint32_t ob = p.off_bits, om = (1u << ob) - 1u;
+    const uint32_t ob = p.off_bits, om = (1u << ob) - 1u, n_re = p.n_re;
     const int mode = p.mode;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     int64_t sl = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -323,13 +337,16 @@ __global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2) cache_pass_kernel(Cach
         for (int v = 0; v < NV; ++v) {
             if constexpr (V::cplx) prev[v] = T{0, 0};
             else prev[v] = 0;
-            if (v < nvec && live && mode >= 2) prev[v] = y[(int64_t)v * D + row];
+            if (PREV && v < nvec && live) prev[v] = y[(int64_t)v * D + row];
         }
         const uint32_t st = warp_excl_scan(my, lane);
         const uint32_t* __restrict__ pe = p.ent + bo + st;
         R accr[NV], acci[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) { accr[v] = 0; acci[v] = 0; }
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (V::cplx) { accr[v] = prev[v].x; acci[v] = prev[v].y; }
+            else { accr[v] = prev[v]; acci[v] = 0; }
+        }
         auto add = [&](uint32_t w) {
             const int64_t j = p.xoff + (int64_t)(w & om);
             const CT cf = ctab[w >> ob];
@@ -338,6 +355,11 @@ __global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2) cache_pass_kernel(Cach
                 if (v < nvec) {
                     if constexpr (!V::cplx) {
                         accr[v] += cf * x[(int64_t)v * D + j];
+                    } else if constexpr (AX) {
+                        const T xj = x[(int64_t)v * D + j];
+                        const bool im = (w >> ob) >= n_re;
+                        accr[v] += cf.x * (im ? xj.y : xj.x);
+                        acci[v] += cf.y * (im ? xj.x : xj.y);
                     } else {
                         const T xj = x[(int64_t)v * D + j];
                         accr[v] += cf.x * xj.x - cf.y * xj.y;
@@ -363,27 +385,17 @@ __global__ void __launch_bounds__(BLOCK, NV == 1 ? 8 : 2) cache_pass_kernel(Cach
             if (v >= nvec) continue;
             const int64_t o = (int64_t)v * D + row;
             if constexpr (!V::cplx) {
-                if (mode == 0) y[o] = accr[v] * inv + dg * x[o];
-                else if (mode == 1) y[o] = accr[v];
-                else if (mode == 2) y[o] = prev[v] + accr[v];
-                else y[o] = (prev[v] + accr[v]) * inv + dg * x[o];
+                if (mode == 0 || mode == 3) y[o] = accr[v] * inv + dg * x[o];
+                else y[o] = accr[v];
             } else {
                 T out;
                 if (mode == 0 || mode == 3) {
-                    R sr = accr[v], si = acci[v];
-                    if (mode == 3) {
-                        sr = prev[v].x + sr;
-                        si = prev[v].y + si;
-                    }
                     const T xi = x[o];
-                    out.x = sr * inv + dg * xi.x;
-                    out.y = si * inv + dg * xi.y;
-                } else if (mode == 1) {
+                    out.x = accr[v] * inv + dg * xi.x;
+                    out.y = acci[v] * inv + dg * xi.y;
+                } else {
                     out.x = accr[v];
                     out.y = acci[v];
-                } else {
-                    out.x = prev[v].x + accr[v];
-                    out.y = prev[v].y + acci[v];
                 }
                 y[o] = out;
             }
@@ -508,12 +520,18 @@ static ed_status build_dispatch(const CacheBuild& c, size_t smem, int n_sub, boo
     return ch ? go(uint32_t{}, std::true_type{}) : go(uint32_t{}, std::false_type{});
 }
 
-template <int K>
+template <int K, bool AX = false>
 static ed_status launch_pass(const CachePass& p, int nvec, int sms, cudaStream_t s) {
     const int64_t blocks_needed = (p.ns + (BLOCK / 32) - 1) / (BLOCK / 32);
-    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)sms * 8));
-    if (nvec == 1) cache_pass_kernel<K, 1><<<grid, BLOCK, 0, s>>>(p);
-    else cache_pass_kernel<K, MAXV><<<grid, BLOCK, 0, s>>>(p);
+    const int per_sm = pass_blocks(K, nvec == 1 ? 1 : MAXV);
+    const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, (int64_t)sms * per_sm));
+    if (p.mode >= 2) {
+        if (nvec == 1) cache_pass_kernel<K, 1, AX, true><<<grid, BLOCK, 0, s>>>(p);
+        else cache_pass_kernel<K, MAXV, AX, true><<<grid, BLOCK, 0, s>>>(p);
+    } else {
+        if (nvec == 1) cache_pass_kernel<K, 1, AX, false><<<grid, BLOCK, 0, s>>>(p);
+        else cache_pass_kernel<K, MAXV, AX, false><<<grid, BLOCK, 0, s>>>(p);
+    }
     ED_CUDA(cudaGetLastError());
     return ED_OK;
 }
@@ -732,6 +750,42 @@ ed_status cache_build(ed_hamiltonian* h, ed_dtype dtype, int seg_log2, size_t ma
         ++n_code;
     }
     c.n_code = n_code;
+    // real coefficients first (complex kinds: codes below n_re), then the others
+    {
+        std::vector<int> order, to(n_code);
+        for (int k = 0; k < n_code; ++k)
+            if (c_d2[2 * k + 1] == 0.0) order.push_back(k);
+        c.n_re = (int)order.size();
+        for (int k = 0; k < n_code; ++k)
+            if (c_d2[2 * k + 1] != 0.0) order.push_back(k);
+        for (int k = 0; k < n_code; ++k) to[order[k]] = k;
+        auto permute = [&](auto& v, int w) {
+            auto u = v;
+            for (int k = 0; k < n_code; ++k)
+                for (int e = 0; e < w; ++e) v[(size_t)to[k] * w + e] = u[(size_t)k * w + e];
+        };
+        permute(c_d, 1);
+        permute(c_f, 1);
+        permute(c_d2, 2);
+        permute(c_f2, 2);
+        if (n_code > 0)
+            for (auto& cd : code) cd = (uint8_t)to[cd];  // keys that do not occur keep a valid code
+    }
+    // axis-aligned tables: (c, c) for a real c, (-c, c) for i c
+    std::vector<double> a_d2(2 * NCODE, 0.0);
+    std::vector<float> a_f2(2 * NCODE, 0.f);
+    c.axis_d = c.axis_f = true;
+    for (int k = 0; k < n_code; ++k) {
+        const bool re = k < c.n_re;
+        c.axis_d = c.axis_d && (re || c_d2[2 * k] == 0.0);
+        c.axis_f = c.axis_f && (re ? c_f2[2 * k + 1] == 0.f : c_f2[2 * k] == 0.f);
+        const double vd = re ? c_d2[2 * k] : c_d2[2 * k + 1];
+        const float vf = re ? c_f2[2 * k] : c_f2[2 * k + 1];
+        a_d2[2 * k] = re ? vd : -vd;
+        a_d2[2 * k + 1] = vd;
+        a_f2[2 * k] = re ? vf : -vf;
+        a_f2[2 * k + 1] = vf;
+    }
     int code_bits = 1;
     while ((1 << code_bits) < n_code) ++code_bits;
     c.off_bits = 32 - code_bits;
@@ -739,7 +793,7 @@ ed_status cache_build(ed_hamiltonian* h, ed_dtype dtype, int seg_log2, size_t ma
         return give_up(fail(ED_ERR_TABLE_TOO_LARGE, "%d coefficient codes leave %d bits of column offset, fewer than "
                             "the %d segment bits", n_code, c.off_bits, bits));
     cb.off_bits = c.off_bits;
-    c.ctab.bytes = (size_t)NCODE * (8 + 4 + 16 + 8);
+    c.ctab.bytes = (size_t)NCODE * (16 + 8 + 8 + 4 + 16 + 8);
     c.ctab.p = A.get(c.ctab.bytes, s);
     if (!c.ctab.p) return give_up(fail(ED_ERR_NOMEM, "coefficient table"));
     uint8_t* ct = (uint8_t*)c.ctab.p;
@@ -747,6 +801,8 @@ ed_status cache_build(ed_hamiltonian* h, ed_dtype dtype, int seg_log2, size_t ma
     ED_CUDA(cudaMemcpyAsync(ct + NCODE * 16, c_d.data(), NCODE * 8, cudaMemcpyHostToDevice, s));
     ED_CUDA(cudaMemcpyAsync(ct + NCODE * 24, c_f2.data(), NCODE * 8, cudaMemcpyHostToDevice, s));
     ED_CUDA(cudaMemcpyAsync(ct + NCODE * 32, c_f.data(), NCODE * 4, cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(ct + NCODE * 36, a_d2.data(), NCODE * 16, cudaMemcpyHostToDevice, s));
+    ED_CUDA(cudaMemcpyAsync(ct + NCODE * 52, a_f2.data(), NCODE * 8, cudaMemcpyHostToDevice, s));
     ED_CUDA(cudaMemcpyAsync(d_code, code.data(), (size_t)n_keys, cudaMemcpyHostToDevice, s));
     // per-slice offsets of every segment
     uint32_t* d_tot = (uint32_t*)sc.get((size_t)nb * ns * 4);
@@ -830,8 +886,8 @@ ed_status cache_apply(const ed_hamiltonian* h, ed_dtype dt, const void* x, void*
     switch (dt) {
         case ED_F64: p.ctab = ct + NCODE * 16; p.isq = sq + (size_t)G1 * 8; break;
         case ED_F32: p.ctab = ct + NCODE * 32; p.isq = sqf + (size_t)G1 * 4; break;
-        case ED_C128: p.ctab = ct; p.isq = sq + (size_t)G1 * 8; break;
-        case ED_C64: p.ctab = ct + NCODE * 24; p.isq = sqf + (size_t)G1 * 4; break;
+        case ED_C128: p.ctab = c.axis_d ? ct + NCODE * 36 : ct; p.isq = sq + (size_t)G1 * 8; break;
+        case ED_C64: p.ctab = c.axis_f ? ct + NCODE * 52 : ct + NCODE * 24; p.isq = sqf + (size_t)G1 * 4; break;
         default: return fail(ED_ERR_ARG, "bad dtype");
     }
     for (int k = 0; k < c.nb; ++k) {
@@ -841,12 +897,13 @@ ed_status cache_apply(const ed_hamiltonian* h, ed_dtype dt, const void* x, void*
         p.xoff = (int64_t)k << c.seg_bits;
         p.mode = c.nb == 1 ? 0 : (k == 0 ? 1 : (k == c.nb - 1 ? 3 : 2));
         p.off_bits = (uint32_t)c.off_bits;
+        p.n_re = (uint32_t)c.n_re;
         ed_status st = ED_OK;
         switch (dt) {
             case ED_F64: st = launch_pass<0>(p, nvec, c.sms, s); break;
             case ED_F32: st = launch_pass<1>(p, nvec, c.sms, s); break;
-            case ED_C128: st = launch_pass<2>(p, nvec, c.sms, s); break;
-            case ED_C64: st = launch_pass<3>(p, nvec, c.sms, s); break;
+            case ED_C128: st = c.axis_d ? launch_pass<2, true>(p, nvec, c.sms, s) : launch_pass<2>(p, nvec, c.sms, s); break;
+            case ED_C64: st = c.axis_f ? launch_pass<3, true>(p, nvec, c.sms, s) : launch_pass<3>(p, nvec, c.sms, s); break;
         }
         if (st != ED_OK) return st;
     }

@@ -146,6 +146,8 @@ namespace ed {
 struct HCache {
     bool valid = false;
     int seg_bits = 0, nb = 0, n_code = 0, sms = 0, off_bits = 24;
+    bool axis_d = false, axis_f = false;  // complex codes all real or purely imaginary (FP64 / FP32 table)
+    int n_re = 0;                         // codes below n_re have real coefficients
     int64_t ns = 0;                 // slices of 32 rows
     DevBuf counts, boff, ent, diag, ctab, ctr;
     std::vector<uint64_t> bbase;    // [nb+1] first entry of each segment

@@ -11,10 +11,10 @@ as a library step.  Nothing here touches the CUDA library.
     python tests/golden/make_eigenvalues.py [square32_A1] [square32_E1] [triangular24]
 
 With no arguments every set is computed.  Existing entries of the JSON file
-for sets not named are kept.  Runtime on 8 host cores: about an hour for each
-32-site sector (the brute-force representatives apply all 256 or 128 group
-elements to every one of the C(32,16) = 6.0e8 states), a few minutes for the
-36 triangular sectors.
+for sets not named are kept.  Runtime on 8 host cores: one to two hours for
+each 32-site sector (the brute-force representatives apply all 256 or 128
+group elements to every one of the C(32,16) = 6.0e8 states; the matrix takes
+about twenty minutes more), a few minutes for the 36 triangular sectors.
 """
 from __future__ import annotations
 

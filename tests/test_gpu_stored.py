@@ -149,6 +149,48 @@ def test_stored_many_segments_vs_oracle(P, name):
                 assert np.all(err <= _bound(H, xv, eps) * fac), (name, nvec, single, v, err.max())
 
 
+# Complex vectors on Hamiltonians whose stored coefficients are each real or purely
+# imaginary (the two-multiply-add path of the pass kernel): a real Hamiltonian with complex
+# vectors (all codes real), and a chirality-only kagome model at Gamma (all off-diagonal
+# codes imaginary).  kagome12 with J1 and J_chi together has general complex codes.
+AXIS = {
+    "chain14_TRZ2_odd": lambda: C.chain(14, 1.0, 0.4, translations=True, reflection=True, spinflip=-1, irrep="A2"),
+    "kagome12_chirality_only": lambda: C.kagome([[2, 0], [0, 2]], 0.0, 0.0, 0.3, irrep="A", point="none"),
+    "kagome12_general": lambda: C.kagome([[2, 0], [0, 2]], 1.0, 0.0, 0.3, irrep="A", point="none"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(AXIS))
+def test_stored_complex_vectors_axis_codes(P, name):
+    """Complex FP64 and FP32 vectors, one and about eight segments, 1 and 5 vectors: y
+    against the oracle's matrix within the bound of the other stored tests."""
+    import torch
+    p = AXIS[name]()
+    reps, stab = oracle.basis(p.sector)
+    H = oracle.csr(p, reps, stab)
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    assert h.is_real == (name == "chain14_TRZ2_odd")
+    for seg in (0, _many_segments(b.dim)):
+        for single in (False, True):
+            tdt = torch.complex64 if single else torch.complex128
+            h.store(P.ED_C64 if single else P.ED_C128, seg_log2=seg)
+            for nvec in (1, 5):
+                X = _vectors(reps, True, nvec, 60 + nvec)
+                Xd = X.astype(np.complex64) if single else X
+                eps, fac = (EPS32, 4) if single else (EPS64, 1)
+                x = torch.tensor(Xd if nvec > 1 else Xd[0], dtype=tdt, device="cuda")
+                y = torch.empty_like(x)
+                h.apply(x, y)
+                torch.cuda.synchronize()
+                Y = y.cpu().numpy().reshape(nvec, -1).astype(np.complex128)
+                for v in range(nvec):
+                    xv = Xd[v].astype(np.complex128)
+                    err = np.abs(Y[v] - H @ xv)
+                    assert np.all(err <= _bound(H, xv, eps) * fac), (name, seg, single, nvec, v, err.max())
+            h.store_free()
+
+
 def test_stored_fp32_one_segment_bitexact(P):
     """Real FP32 vectors with one segment: bit-identical to the matrix-free kernel."""
     import torch
