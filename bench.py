@@ -58,7 +58,8 @@ def peaks():
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("ed_apply.cu", "ed_apply_impl.cuh", "ed_device.cuh", "ed_internal.h", "ed_cache.cu"):
+    for f in ("ed_apply.cu", "ed_apply_impl.cuh", "ed_device.cuh", "ed_internal.h", "ed_cache.cu", "ed_cache.cuh",
+              "ed_cache_lanes.cu"):
         h.update(open(os.path.join(ROOT, "paper_2210_03511_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -324,19 +325,22 @@ def workload_summary(pkg, torch, name, dtypes, stream, flush, steps=10, warmup=3
         t_s, t_f = statistics.mean(ms) / 1e3, statistics.mean(ms_free) / 1e3
         out[dtype] = {"ms_per_step": t_s * 1e3, "value": D * n_terms / t_s / 1e9, "unit": UNIT,
                       "frac": stored_bytes(D, G, s_x) / t_s / 1e9 / peak,
-                      "store": {"autotune_seconds": round(t_store, 3), "seg_log2": seg, "bytes": info["bytes"],
+                      "store": {"autotune_seconds": round(t_store, 3), "seg_log2": seg,
+                                "lanes_per_row": H.store_schedule()["lanes_per_row"], "bytes": info["bytes"],
                                 "segments": info["segments"], "codes": info["codes"]},
                       "matrix_free": {"ms_per_step": t_f * 1e3, "value": D * n_terms / t_f / 1e9,
                                       "frac": matrix_free_bytes(D, G, s_x, s_st) / t_f / 1e9 / peak}}
         H.store_free()
         del x, y
         torch.cuda.empty_cache()
-    seg_of = {_edt(pkg, dt): out[dt]["store"]["seg_log2"] for dt in dtypes}
+    seg_of = {_edt(pkg, dt): (out[dt]["store"]["seg_log2"], out[dt]["store"]["lanes_per_row"]) for dt in dtypes}
 
-    def store_for(edt):  # the structure with the segment size tuned for this dtype
+    def store_for(edt):  # the structure with the schedule tuned for this dtype
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H.store(edt, seg_log2=seg_of[edt], stream=stream)
+        H.store(edt, seg_log2=seg_of[edt][0], stream=stream)
+        if seg_of[edt][1] > 1:
+            H.store_set_lanes(seg_of[edt][1])
         torch.cuda.synchronize()
         return time.perf_counter() - t0
 
@@ -456,6 +460,10 @@ def main():
     ap.add_argument("--matrix-free", action="store_true", help="time the matrix-free kernel only (no stored structure)")
     ap.add_argument("--seg-log2", type=int, default=0,
                     help="log2 column-segment size of the stored structure (0: the library's default)")
+    ap.add_argument("--lanes", type=int, default=0,
+                    help="lanes per row of the stored pass (1, 2, 4, 8; with --seg-log2 or alone: no autotuning)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="the library's default schedule instead of ed_hamiltonian_store_autotune's choice")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     args = ap.parse_args()
@@ -529,12 +537,22 @@ def main():
     if not args.matrix_free:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H.store(edt, seg_log2=args.seg_log2, stream=stream)
+        autotune = not (args.no_autotune or args.seg_log2 or args.lanes)
+        if autotune:  # segment size and lanes per row chosen by timing (outside the timed region)
+            H.store_autotune(edt, stream=stream)
+        else:
+            H.store(edt, seg_log2=args.seg_log2, stream=stream)
+            if args.lanes > 1:
+                H.store_set_lanes(args.lanes)
         torch.cuda.synchronize()
         t_store = time.perf_counter() - t0
         info = H.store_info()
+        sch = H.store_schedule()
         store = {"seconds": round(t_store, 3), "bytes": info["bytes"], "segments": info["segments"],
-                 "codes": info["codes"], "entries": info["entries"], "seg_log2": args.seg_log2 or "default"}
+                 "codes": info["codes"], "entries": info["entries"],
+                 "seg_log2": sch["seg_log2"], "lanes_per_row": sch["lanes_per_row"],
+                 "schedule": "autotuned (ed_hamiltonian_store_autotune)" if autotune else
+                             ("given" if args.seg_log2 or args.lanes else "library default")}
     gpu_index = local
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     if cvd and cvd.replace(",", "").isdigit():
@@ -583,7 +601,8 @@ def main():
     if args.matrix_free:
         b_alg, kernel = b_free, "hx_kernel"
     else:
-        b_alg, kernel = stored_bytes(D, gathers, s_x), "cache_pass_kernel"
+        b_alg = stored_bytes(D, gathers, s_x)
+        kernel = "cache_pass_lanes" if store["lanes_per_row"] > 1 else "cache_pass_kernel"
     achieved = b_alg / t_launch / 1e9
     traffic, ncu_ctx = profiled_traffic(args.workload, dtype, kernel)
     launches_per_step = 1 if args.matrix_free else store["segments"]
@@ -594,7 +613,8 @@ def main():
                        "n_sublat": int(problem.sector.n_sublat),
                        "l2": "flushed: 256 MB write between timed steps (inputs also exceed L2)",
                        "hx_path": "matrix-free" if args.matrix_free else
-                       "stored structure (ed_hamiltonian_store, built once per Hamiltonian, outside the timed region)",
+                       "stored structure (built once per Hamiltonian with the schedule in `store`, outside the "
+                       "timed region)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
                        "basis_build_s": round(t_basis, 3)},
             "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -332,16 +332,37 @@ ed_status ed_hamiltonian_store(ed_hamiltonian* h, ed_dtype dtype, int32_t seg_lo
                                ed_stream stream, size_t* bytes);
 
 /* ed_hamiltonian_store_autotune -- ed_hamiltonian_store with the column
- * segment chosen by timing: the structure is built for segments of 64, 128 and
- * 256 MB of `dtype` elements (within 2^5..2^24 elements and 128 segments), one
- * ed_apply of each is timed on scratch vectors (2 D elements of `dtype` from
- * the basis's allocator, released on return), and the fastest is kept (built
- * again if it was not the last one tried).  Fewer, larger segments save the
- * per-row work of each pass; smaller ones keep the gathered part of x in L2.
+ * segment and the one-vector schedule chosen by timing: the structure is built
+ * for segments of half, one and two times the default size (within
+ * 2^5..2^26 elements and 128 segments); for each, one-vector ed_apply is timed on
+ * scratch vectors (2 D elements of `dtype` from the basis's allocator,
+ * released on return) with 1, 2, 4 and 8 lanes per row
+ * (ed_hamiltonian_store_set_lanes), and the fastest pair is kept (the
+ * structure built again if it was not the last one tried).  Fewer, larger
+ * segments save the per-row work of each pass; smaller ones keep the gathered
+ * part of x in L2; several lanes per row balance long rows across a warp.
  * *seg_log2 (if non-NULL) receives the chosen log2 segment size, *bytes the
- * structure's size.  Errors as ed_hamiltonian_store.  Synchronous. */
+ * structure's size (ed_hamiltonian_store_schedule reports both choices).
+ * Errors as ed_hamiltonian_store.  Synchronous. */
 ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype dtype, size_t max_bytes, ed_stream stream,
                                         int32_t* seg_log2, size_t* bytes);
+
+/* ed_hamiltonian_store_set_lanes -- work split of the stored pass for ONE
+ * vector (several vectors always take one lane per row): lanes_per_row = 1
+ * (the default after every ed_hamiltonian_store: one lane per row, a row's
+ * elements summed in stored order, one warp per 32 rows) or 2, 4, 8 (groups of
+ * that many consecutive lanes share a row; element k goes to lane k mod L of
+ * the group and a butterfly of warp shuffles combines the lanes' sums; a warp
+ * still owns 32 rows and takes them in L rounds).  Results differ from one
+ * lane per row only by summation order (the bit-identity with the
+ * matrix-free kernel holds for one lane per row).  ED_ERR_ARG for other
+ * values or without a stored structure. */
+ed_status ed_hamiltonian_store_set_lanes(ed_hamiltonian* h, int32_t lanes_per_row);
+
+/* The stored structure's schedule: log2 column-segment size and lanes per row
+ * of the one-vector pass (both 0 without a stored structure).  Either pointer
+ * may be NULL. */
+ed_status ed_hamiltonian_store_schedule(const ed_hamiltonian* h, int32_t* seg_log2, int32_t* lanes_per_row);
 
 /* Size of the stored structure: entries (off-diagonal elements), column
  * segments, distinct coefficient codes, device bytes; all 0 when none. */
@@ -518,7 +539,9 @@ typedef struct {
     ed_dtype dtype;        /* ED_F64 (all sectors real) or ED_C128 */
     int32_t block;         /* right-hand sides per sector, 1..8 */
     int32_t n_eig;         /* lowest eigenvalues per sector */
-    double tol;            /* relative change of each eigenvalue between checks */
+    double tol;            /* convergence: each eigenvalue changed by at most tol/10 (relative) since the
+                              previous check, on two checks in a row; with block = 1 also the Ritz
+                              residual bound r = beta |s_last| within min(r, r^2/gap) <= tol (relative) */
     int32_t max_iter;      /* block steps at most (2..400) */
     uint64_t seed;         /* Gaussian start blocks from keyed SplitMix64 of (seed, column, state) */
     int32_t use_graph;     /* 1: capture one step (all kernels, all sectors) as a CUDA graph and replay it */

@@ -12,7 +12,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libed.so")
 SOURCES = ["ed_host.cpp", "ed_basis.cu", "ed_apply.cu", "ed_apply_k0.cu", "ed_apply_k1.cu", "ed_apply_k2.cu",
-           "ed_apply_k3.cu", "ed_lanczos.cu", "ed_batch.cu", "ed_cache.cu"]
+           "ed_apply_k3.cu", "ed_lanczos.cu", "ed_batch.cu", "ed_cache.cu", "ed_cache_lanes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -382,13 +382,6 @@ static std::vector<double> band_lowest(const Band& T, int m) {
 // reorthogonalisation the plain values; the plain recursion (blocks of one:
 // a tridiagonal T with diagonal a1, off-diagonal b1) removes the spurious
 // copies of converged values as ed_lanczos does.
-static std::vector<double> sector_lowest(const Band& T, int k, bool filtered, const std::vector<double>& a1,
-                                         const std::vector<double>& b1) {
-    if (!filtered) return band_lowest(T, k);
-    std::vector<double> lam;
-    tridiag_lowest(a1, b1, T.n, k, true, 2.220446049250313e-16, lam);
-    return lam;
-}
 
 // ------------------------------------------------------------------ batch construction and apply
 static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n) {
@@ -795,19 +788,37 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
                         for (int c = 0; c < b; ++c) put((j + 1) * b + r, j * b + c, cd(Bj[r * b + c].x, Bj[r * b + c].y));
                 }
             }
-            std::vector<double> a1, b1;
-            if (local) {  // blocks of one
-                a1.resize(nk2);
-                b1.assign(nk2, 0.0);
+            // converged: every wanted value changed by at most tol/10 (relative)
+            // since the last check, on two checks in a row; with blocks of one
+            // also a small residual bound r = beta |s_last| of the Ritz pair
+            // (eigenvalue error at most min(r, r^2/gap)), as in ed_lanczos
+            std::vector<double> lam, last;
+            bool ok;
+            if (b == 1) {
+                std::vector<double> a1(nk2), b1(nk2, 0.0);
                 for (int i = 0; i < nk2; ++i) a1[i] = T.get(i, 0).real();
                 for (int i = 0; i + 1 < nk2; ++i) b1[i] = std::abs(T.get(i + 1, 1));
+                tridiag_lowest(a1, b1, nk2, n_eig + 1, local != 0, 2.220446049250313e-16, lam, &last);
+                const double2 bl = Bh[((size_t)sct * kcap + iters - 1) * bb];
+                const double bh = nk2 < nt2 ? 0.0 : std::abs(cd(bl.x, bl.y));  // a collapsed column: invariant
+                ok = (int)lam.size() >= n_eig;
+                for (int e = 0; e < n_eig && ok; ++e) {
+                    const double sc = std::max(1.0, fabs(lam[e]));
+                    double gap = 1e300;
+                    for (int q = 0; q < (int)lam.size(); ++q)
+                        if (q != e) gap = std::min(gap, fabs(lam[q] - lam[e]));
+                    const double rb = bh * fabs(last[e]);
+                    if (!(rb <= o->tol * sc || rb * rb <= o->tol * sc * gap)) ok = false;
+                }
+                if ((int)lam.size() > n_eig) lam.resize(n_eig);
+            } else {
+                lam = band_lowest(T, n_eig);
+                ok = (int)lam.size() == n_eig;
             }
-            const std::vector<double> lam = sector_lowest(T, n_eig, local, a1, b1);
-            bool ok = (int)lam.size() == n_eig;
             for (int e = 0; e < (int)lam.size(); ++e) {
                 cur[sct][e] = lam[e];
                 const double sc = std::max(1.0, fabs(lam[e]));
-                if (fabs(lam[e] - prev[sct][e]) > o->tol * sc) ok = false;
+                if (fabs(lam[e] - prev[sct][e]) > 0.1 * o->tol * sc) ok = false;
             }
             steady[sct] = ok ? steady[sct] + 1 : 0;
             prev[sct] = cur[sct];

@@ -31,14 +31,13 @@
 #include <algorithm>
 #include <vector>
 
-#include "ed_apply_impl.cuh"
+#include "ed_cache.cuh"
 
 namespace ed {
 
 namespace {
 
 constexpr int CMAXNB = 128;   // column segments at most
-constexpr int NCODE = 256;    // coefficient codes at most (one byte)
 
 struct CacheBuild {
     HxArgs a;                      // basis and terms (x, y unused)
@@ -58,33 +57,6 @@ struct CacheBuild {
     const uint8_t* code;           // key -> code               (pass 1)
     unsigned long long* counters;  // [0] entries, [1] incompatible images, [2] missing, [3] overflow
 };
-
-// Arguments of one segment's pass of the stored-structure H.x.
-struct CachePass {
-    const uint8_t* counts;   // [Dpad] entries per row in this segment
-    const uint32_t* boff;    // [ns] first entry of each slice, relative to `ent`
-    const uint32_t* ent;     // this segment's entries
-    const void* x;           // [nvec][D]
-    void* y;                 // [nvec][D]
-    const void* ctab;        // [256] coefficients of the value kind (R, or T for complex kinds)
-    const void* isq;         // [G+1] 1/sqrt(k) of the value kind's real type
-    const uint16_t* stab;    // [D] |Stab sigma_i|
-    const double* diag;      // [D] Ising part
-    int64_t D, ns, xoff;     // xoff: first column of the segment
-    int nvec, mode;
-    uint32_t off_bits;       // entry = (code << off_bits) | column offset
-    uint32_t n_re;           // codes below n_re have real coefficients (complex kinds)
-};
-
-__device__ __forceinline__ uint32_t warp_excl_scan(uint32_t v, int lane) {
-    uint32_t s = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t u = __shfl_up_sync(0xffffffffu, s, o);
-        if (lane >= o) s += u;
-    }
-    return s - v;
-}
 
 // One pass of the structure build over all rows, one warp per slice of 32
 // rows (the per-slice offsets of pass 1 need the whole warp).  The row walk
@@ -274,10 +246,6 @@ __global__ void slice_offsets(const uint64_t* abs_off, int64_t ns, int nb, uint3
         if (i == b * ns) bbase[b] = abs_off[i];
     }
 }
-
-// Resident blocks per SM of a pass launch: 32 registers a thread for one
-// vector (complex FP64 takes 40 to keep its accumulators out of local memory).
-constexpr int pass_blocks(int K, int NV) { return NV == 1 ? (K == 2 ? 6 : 8) : 2; }
 
 // One segment's pass of y = H x from the stored structure: one warp per
 // slice of 32 rows, one lane per row.  With tens of segments a row has only a
@@ -883,11 +851,13 @@ ed_status cache_apply(const ed_hamiltonian* h, ed_dtype dt, const void* x, void*
     const uint8_t* sq = b->dt.blob + b->dt.off_sqrt;    // sqrt(k), then 1/sqrt(k), k = 0..G (double)
     const uint8_t* sqf = b->dt.blob + b->dt.off_sqrtf;  // the same in float
     const int G1 = b->ht.G + 1;
+    const bool lanes = nvec == 1 && c.lanes > 1;  // several lanes per row: the general tables
+    const bool ax_d = c.axis_d && !lanes, ax_f = c.axis_f && !lanes;
     switch (dt) {
         case ED_F64: p.ctab = ct + NCODE * 16; p.isq = sq + (size_t)G1 * 8; break;
         case ED_F32: p.ctab = ct + NCODE * 32; p.isq = sqf + (size_t)G1 * 4; break;
-        case ED_C128: p.ctab = c.axis_d ? ct + NCODE * 36 : ct; p.isq = sq + (size_t)G1 * 8; break;
-        case ED_C64: p.ctab = c.axis_f ? ct + NCODE * 52 : ct + NCODE * 24; p.isq = sqf + (size_t)G1 * 4; break;
+        case ED_C128: p.ctab = ax_d ? ct + NCODE * 36 : ct; p.isq = sq + (size_t)G1 * 8; break;
+        case ED_C64: p.ctab = ax_f ? ct + NCODE * 52 : ct + NCODE * 24; p.isq = sqf + (size_t)G1 * 4; break;
         default: return fail(ED_ERR_ARG, "bad dtype");
     }
     for (int k = 0; k < c.nb; ++k) {
@@ -899,11 +869,15 @@ ed_status cache_apply(const ed_hamiltonian* h, ed_dtype dt, const void* x, void*
         p.off_bits = (uint32_t)c.off_bits;
         p.n_re = (uint32_t)c.n_re;
         ed_status st = ED_OK;
-        switch (dt) {
-            case ED_F64: st = launch_pass<0>(p, nvec, c.sms, s); break;
-            case ED_F32: st = launch_pass<1>(p, nvec, c.sms, s); break;
-            case ED_C128: st = c.axis_d ? launch_pass<2, true>(p, nvec, c.sms, s) : launch_pass<2>(p, nvec, c.sms, s); break;
-            case ED_C64: st = c.axis_f ? launch_pass<3, true>(p, nvec, c.sms, s) : launch_pass<3>(p, nvec, c.sms, s); break;
+        if (lanes) {
+            st = launch_pass_lanes(p, dt == ED_F64 ? 0 : dt == ED_F32 ? 1 : dt == ED_C128 ? 2 : 3, c.lanes, c.sms, s);
+        } else {
+            switch (dt) {
+                case ED_F64: st = launch_pass<0>(p, nvec, c.sms, s); break;
+                case ED_F32: st = launch_pass<1>(p, nvec, c.sms, s); break;
+                case ED_C128: st = ax_d ? launch_pass<2, true>(p, nvec, c.sms, s) : launch_pass<2>(p, nvec, c.sms, s); break;
+                case ED_C64: st = ax_f ? launch_pass<3, true>(p, nvec, c.sms, s) : launch_pass<3>(p, nvec, c.sms, s); break;
+            }
         }
         if (st != ED_OK) return st;
     }
@@ -947,6 +921,26 @@ extern "C" void ed_hamiltonian_store_free(ed_hamiltonian* h) {
 // partial sum, so fewer, larger segments pay where rows are many (the 40-site
 // square sector prefers 128 MB of FP64) and smaller ones where the gathers
 // dominate (the 36-site kagome sector, complex FP32, prefers 64 MB).
+extern "C" ed_status ed_hamiltonian_store_set_lanes(ed_hamiltonian* h, int32_t lanes_per_row) {
+    using namespace ed;
+    if (!h) return fail(ED_ERR_ARG, "null argument");
+    if (!h->cache.valid) return fail(ED_ERR_ARG, "no stored structure");
+    if (lanes_per_row != 1 && lanes_per_row != 2 && lanes_per_row != 4 && lanes_per_row != 8)
+        return fail(ED_ERR_ARG, "lanes per row must be 1, 2, 4 or 8");
+    h->cache.lanes = lanes_per_row;
+    return ED_OK;
+}
+
+extern "C" ed_status ed_hamiltonian_store_schedule(const ed_hamiltonian* h, int32_t* seg_log2,
+                                                   int32_t* lanes_per_row) {
+    using namespace ed;
+    if (!h) return fail(ED_ERR_ARG, "null argument");
+    const bool v = h->cache.valid;
+    if (seg_log2) *seg_log2 = v ? h->cache.seg_bits : 0;
+    if (lanes_per_row) *lanes_per_row = v ? h->cache.lanes : 0;
+    return ED_OK;
+}
+
 extern "C" ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype dtype, size_t max_bytes,
                                                    ed_stream stream, int32_t* seg_log2, size_t* bytes) {
     using namespace ed;
@@ -960,7 +954,7 @@ extern "C" ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype d
     const int b0 = default_seg_bits(dtype);
     std::vector<int> cands;
     for (int b = b0 - 1; b <= b0 + 1; ++b)
-        if (b >= 5 && b <= 24 && (((uint64_t)D + ((uint64_t)1 << b) - 1) >> b) <= (uint64_t)CMAXNB) cands.push_back(b);
+        if (b >= 5 && b <= 26 && (((uint64_t)D + ((uint64_t)1 << b) - 1) >> b) <= (uint64_t)CMAXNB) cands.push_back(b);
     if (cands.empty()) cands.push_back(b0);
     const size_t sx = dtype == ED_F32 ? 4 : dtype == ED_C128 ? 16 : 8;
     const Alloc& A = h->basis->alloc;
@@ -980,24 +974,28 @@ extern "C" ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype d
         }
     } ef{e0, e1};
     float best = 1e30f;
-    int best_b = 0;
+    int best_b = 0, best_l = 1;
     ed_status last = ED_OK;
     for (int b : cands) {
         last = cache_build(h, dtype, b, max_bytes, s);
         if (last == ED_ERR_NOMEM || last == ED_ERR_TABLE_TOO_LARGE || (last == ED_ERR_ARG && b != b0)) continue;
         if (last != ED_OK) return last;
-        ed_status st = cache_apply(h, dtype, x, y, 1, s);  // warm-up
-        if (st != ED_OK) return st;
-        ED_CUDA(cudaEventRecord(e0, s));
-        for (int r = 0; r < 2 && st == ED_OK; ++r) st = cache_apply(h, dtype, x, y, 1, s);
-        if (st != ED_OK) return st;
-        ED_CUDA(cudaEventRecord(e1, s));
-        ED_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        ED_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            best_b = b;
+        for (int l = 1; l <= 8; l *= 2) {
+            h->cache.lanes = l;
+            ed_status st = cache_apply(h, dtype, x, y, 1, s);  // warm-up
+            if (st != ED_OK) return st;
+            ED_CUDA(cudaEventRecord(e0, s));
+            for (int r = 0; r < 2 && st == ED_OK; ++r) st = cache_apply(h, dtype, x, y, 1, s);
+            if (st != ED_OK) return st;
+            ED_CUDA(cudaEventRecord(e1, s));
+            ED_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            ED_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                best_b = b;
+                best_l = l;
+            }
         }
     }
     if (!best_b) {
@@ -1008,6 +1006,7 @@ extern "C" ed_status ed_hamiltonian_store_autotune(ed_hamiltonian* h, ed_dtype d
         const ed_status st = cache_build(h, dtype, best_b, max_bytes, s);
         if (st != ED_OK) return st;
     }
+    h->cache.lanes = best_l;
     if (seg_log2) *seg_log2 = best_b;
     if (bytes) *bytes = h->cache.bytes;
     return ED_OK;

@@ -148,6 +148,7 @@ struct HCache {
     int seg_bits = 0, nb = 0, n_code = 0, sms = 0, off_bits = 24;
     bool axis_d = false, axis_f = false;  // complex codes all real or purely imaginary (FP64 / FP32 table)
     int n_re = 0;                         // codes below n_re have real coefficients
+    int lanes = 1;                        // lanes per row of the one-vector pass (1, 2, 4, 8)
     int64_t ns = 0;                 // slices of 32 rows
     DevBuf counts, boff, ent, diag, ctab, ctr;
     std::vector<uint64_t> bbase;    // [nb+1] first entry of each segment
@@ -265,7 +266,7 @@ ed_status cache_apply(const ed_hamiltonian* h, ed_dtype dt, const void* x, void*
 void cache_free(ed_hamiltonian* h);
 // implemented in ed_lanczos.cu
 void tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b, int n, int k, bool filter,
-                    double eps_v, std::vector<double>& lam);
+                    double eps_v, std::vector<double>& lam, std::vector<double>* last = nullptr);
 ed_status lanczos_run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* evals, void* evecs,
                       ed_lanczos_report* rep, cudaStream_t s);
 }  // namespace ed

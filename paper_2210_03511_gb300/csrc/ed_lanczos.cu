@@ -582,17 +582,24 @@ static void tri_eig_filtered(const std::vector<double>& a, const std::vector<dou
 // Lowest k eigenvalues of the tridiagonal T (diagonal a, off-diagonal b),
 // optionally with the spurious-value filter (eps_v: unit roundoff of the
 // Lanczos vectors); shared with the batched solver and ed_tridiag_eigs.
+// With `last`, also the last component of each eigenvector (times the next
+// beta, the residual norm of the Ritz pair).
 void tridiag_lowest(const std::vector<double>& a, const std::vector<double>& b, int n, int k, bool filter,
-                    double eps_v, std::vector<double>& lam) {
+                    double eps_v, std::vector<double>& lam, std::vector<double>* last) {
     std::vector<std::vector<double>> vec;
     if (!filter) {
         tri_eig(a, b, n, k, lam, vec);
-        return;
+    } else {
+        double tn = 0.0;
+        for (int i = 0; i < n; ++i)
+            tn = std::max(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
+        tri_eig_filtered(a, b, n, k, 100.0 * eps_v * tn, 1e3 * 2.220446049250313e-16 * tn, lam, vec);
     }
-    double tn = 0.0;
-    for (int i = 0; i < n; ++i)
-        tn = std::max(tn, fabs(a[i]) + (i > 0 ? fabs(b[i - 1]) : 0.0) + (i + 1 < n ? fabs(b[i]) : 0.0));
-    tri_eig_filtered(a, b, n, k, 100.0 * eps_v * tn, 1e3 * 2.220446049250313e-16 * tn, lam, vec);
+    if (last) {
+        last->assign(lam.size(), 0.0);
+        for (size_t p = 0; p < lam.size() && p < vec.size(); ++p)
+            if (n > 0 && (int)vec[p].size() >= n) (*last)[p] = vec[p][n - 1];
+    }
 }
 
 // ---------------------------------------------------------------- driver

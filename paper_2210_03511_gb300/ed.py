@@ -108,6 +108,8 @@ def lib():
         L.ed_hamiltonian_store_autotune.argtypes = [c_vp, ctypes.c_int, ctypes.c_size_t, c_vp, P(c_i32),
                                                     P(ctypes.c_size_t)]
         L.ed_hamiltonian_store_free.argtypes = [c_vp]
+        L.ed_hamiltonian_store_set_lanes.argtypes = [c_vp, c_i32]
+        L.ed_hamiltonian_store_schedule.argtypes = [c_vp, P(c_i32), P(c_i32)]
         L.ed_hamiltonian_store_free.restype = None
         L.ed_lanczos.argtypes = [c_vp, P(ed_lanczos_opts), P(c_dbl), c_vp, P(ed_lanczos_report), c_vp]
         L.ed_batch_create.argtypes = [P(c_vp), c_i32, P(c_vp)]
@@ -446,6 +448,16 @@ class Hamiltonian:
         check(lib().ed_hamiltonian_store_info(self.handle, ctypes.byref(e), ctypes.byref(s), ctypes.byref(c),
                                               ctypes.byref(b)))
         return dict(entries=int(e.value), segments=int(s.value), codes=int(c.value), bytes=int(b.value))
+
+    def store_set_lanes(self, lanes_per_row: int):
+        """ed_hamiltonian_store_set_lanes: lanes per row of the one-vector stored pass (1, 2, 4, 8)."""
+        check(lib().ed_hamiltonian_store_set_lanes(self.handle, int(lanes_per_row)))
+
+    def store_schedule(self) -> dict:
+        """ed_hamiltonian_store_schedule: log2 segment size and lanes per row (0, 0 without a structure)."""
+        sl, ln = c_i32(), c_i32()
+        check(lib().ed_hamiltonian_store_schedule(self.handle, ctypes.byref(sl), ctypes.byref(ln)))
+        return dict(seg_log2=int(sl.value), lanes_per_row=int(ln.value))
 
     def store_free(self):
         lib().ed_hamiltonian_store_free(self.handle)

@@ -191,6 +191,71 @@ def test_stored_complex_vectors_axis_codes(P, name):
             h.store_free()
 
 
+LANES_CASES = ["chain16_nosym", "square16_B1_odd", "kagome12_E1", "kagome18_A", "square40_nup3", "chain14_TRZ2_odd"]
+
+
+@pytest.mark.parametrize("name", LANES_CASES)
+def test_stored_lanes_per_row_vs_oracle(P, name):
+    """One-vector pass with 2, 4 and 8 lanes per row (ed_hamiltonian_store_set_lanes), one and
+    about eight segments, FP64 and FP32 kinds (complex vectors on the real chain too): y
+    against the oracle's matrix within the bound of the other stored tests; several vectors
+    keep one lane per row; the schedule query reports the setting."""
+    import torch
+    if name in SMALL:
+        p, reps, stab, H = _oracle(name)
+    else:
+        p = AXIS[name]()
+        reps, stab = oracle.basis(p.sector)
+        H = oracle.csr(p, reps, stab)
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    cplx = not h.is_real or name == "chain14_TRZ2_odd"
+    kinds = [(torch.complex128, P.ED_C128, EPS64, 1), (torch.complex64, P.ED_C64, EPS32, 4)] if cplx else \
+        [(torch.float64, P.ED_F64, EPS64, 1), (torch.float32, P.ED_F32, EPS32, 4)]
+    X = _vectors(reps, cplx, 3, 77)
+    for seg in (0, _many_segments(b.dim)):
+        for tdt, edt, eps, fac in kinds:
+            h.store(edt, seg_log2=seg)
+            assert h.store_schedule()["lanes_per_row"] == 1
+            npdt = {torch.complex64: np.complex64, torch.float32: np.float32}.get(tdt)
+            Xd = X.astype(npdt) if npdt else X
+            for lanes in (2, 4, 8):
+                h.store_set_lanes(lanes)
+                assert h.store_schedule()["lanes_per_row"] == lanes
+                x = torch.tensor(Xd, dtype=tdt, device="cuda")
+                y = torch.empty_like(x)
+                for v in range(3):  # one vector at a time: the lanes schedule
+                    h.apply(x[v], y[v])
+                y3 = torch.empty_like(x)
+                h.apply(x, y3)  # several vectors: one lane per row
+                torch.cuda.synchronize()
+                for yy in (y, y3):
+                    Y = yy.cpu().numpy().astype(np.complex128)
+                    for v in range(3):
+                        xv = Xd[v].astype(np.complex128)
+                        err = np.abs(Y[v] - H @ xv)
+                        assert np.all(err <= _bound(H, xv, eps) * fac), (name, seg, edt, lanes, v, err.max())
+            h.store_free()
+            assert h.store_schedule() == dict(seg_log2=0, lanes_per_row=0)
+
+
+def test_stored_lanes_errors(P):
+    """ed_hamiltonian_store_set_lanes: ED_ERR_ARG without a stored structure and for counts
+    other than 1, 2, 4, 8."""
+    p, reps, stab, H = _oracle("chain16_nosym")
+    b = P.Basis(p.sector)
+    h = P.Hamiltonian(b, p.terms)
+    with pytest.raises(P.EdError) as e:
+        h.store_set_lanes(2)
+    assert e.value.name == "ED_ERR_ARG"
+    h.store()
+    for bad in (0, 3, 16, -1):
+        with pytest.raises(P.EdError) as e:
+            h.store_set_lanes(bad)
+        assert e.value.name == "ED_ERR_ARG"
+    assert h.store_schedule()["lanes_per_row"] == 1
+
+
 def test_stored_fp32_one_segment_bitexact(P):
     """Real FP32 vectors with one segment: bit-identical to the matrix-free kernel."""
     import torch
@@ -246,15 +311,17 @@ def test_stored_limit_refused(P):
 
 
 def test_stored_autotune(P):
-    """The segment-size autotuner keeps one of its candidates (64, 128 or 256 MB of the
-    vector type, here forced to one segment by the small sector), and the kept structure
-    gives the oracle's H x."""
+    """The autotuner keeps one of its segment candidates (half, one and two times the
+    default of 2^24 complex-FP32 elements; one segment for this small sector) and one of
+    the lanes-per-row schedules, and the kept structure gives the oracle's H x."""
     import torch
     p, reps, stab, H = _oracle("kagome18_A")
     b = P.Basis(p.sector)
     h = P.Hamiltonian(b, p.terms)
     seg, nbytes = h.store_autotune(P.ED_C64)
-    assert seg in (22, 23, 24) and nbytes == h.store_info()["bytes"] > 0
+    assert seg in (23, 24, 25) and nbytes == h.store_info()["bytes"] > 0
+    sch = h.store_schedule()
+    assert sch["seg_log2"] == seg and sch["lanes_per_row"] in (1, 2, 4, 8)
     X = state_vector(5, reps, complex_=True)
     x = torch.tensor(X, dtype=torch.complex128, device="cuda")
     y = torch.empty_like(x)
