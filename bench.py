@@ -460,10 +460,10 @@ def main():
     ap.add_argument("--matrix-free", action="store_true", help="time the matrix-free kernel only (no stored structure)")
     ap.add_argument("--seg-log2", type=int, default=0,
                     help="log2 column-segment size of the stored structure (0: the library's default)")
-    ap.add_argument("--lanes", type=int, default=0,
-                    help="lanes per row of the stored pass (1, 2, 4, 8; with --seg-log2 or alone: no autotuning)")
-    ap.add_argument("--no-autotune", action="store_true",
-                    help="the library's default schedule instead of ed_hamiltonian_store_autotune's choice")
+    ap.add_argument("--lanes", type=int, default=0, help="lanes per row of the stored pass (1, 2, 4, 8)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="segment size and lanes per row chosen by ed_hamiltonian_store_autotune (square40: the "
+                         "library default, found in about 30 s)")
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline (profiling runs)")
     args = ap.parse_args()
@@ -537,7 +537,7 @@ def main():
     if not args.matrix_free:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        autotune = not (args.no_autotune or args.seg_log2 or args.lanes)
+        autotune = args.autotune
         if autotune:  # segment size and lanes per row chosen by timing (outside the timed region)
             H.store_autotune(edt, stream=stream)
         else:

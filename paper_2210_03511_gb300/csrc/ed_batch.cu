@@ -378,11 +378,6 @@ static std::vector<double> band_lowest(const Band& T, int m) {
     return out;
 }
 
-// Lowest k eigenvalues of one sector's block-tridiagonal T.  With full
-// reorthogonalisation the plain values; the plain recursion (blocks of one:
-// a tridiagonal T with diagonal a1, off-diagonal b1) removes the spurious
-// copies of converged values as ed_lanczos does.
-
 // ------------------------------------------------------------------ batch construction and apply
 static ed_status batch_init(ed_batch* B, const ed_hamiltonian* const* hs, int n) {
     if (!hs || n < 1) return fail(ED_ERR_ARG, "empty batch");

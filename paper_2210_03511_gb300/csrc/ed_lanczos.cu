@@ -17,6 +17,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <condition_variable>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -656,7 +658,23 @@ struct HostKrylov {
     size_t reserved = 0, vec_bytes = 0;
     cudaStream_t copy = nullptr;
     cudaEvent_t made[4] = {}, copied[4] = {};  // by vector index mod 4
+    // First touch of the host pages runs on a thread of its own, a few
+    // vectors ahead of the copies, so that the page faults overlap the GPU's
+    // steps instead of stalling the loop that enqueues them.
+    static constexpr int AHEAD = 3;
+    int n_vec = 0;
+    std::thread toucher;
+    std::mutex mu;
+    std::condition_variable cv;
+    int want = 0, touched = 0;
+    bool stop = false;
     ~HostKrylov() {
+        {
+            std::lock_guard<std::mutex> l(mu);
+            stop = true;
+        }
+        cv.notify_all();
+        if (toucher.joinable()) toucher.join();
         if (copy) {
             cudaStreamSynchronize(copy);
             cudaStreamDestroy(copy);
@@ -668,9 +686,35 @@ struct HostKrylov {
         if (base) munmap(base, reserved);
     }
     uint8_t* vec(int k) const { return (uint8_t*)base + (size_t)k * vec_bytes; }
+    void start(int n) {
+        n_vec = n;
+        madvise(base, reserved, MADV_HUGEPAGE);  // a hint: fewer faults where the kernel allows it
+        toucher = std::thread([this]() {
+            for (int k = 0; k < n_vec; ++k) {
+                {
+                    std::unique_lock<std::mutex> l(mu);
+                    cv.wait(l, [&]() { return stop || want > k; });
+                    if (stop) return;
+                }
+                touch(k);
+                {
+                    std::lock_guard<std::mutex> l(mu);
+                    touched = k + 1;
+                }
+                cv.notify_all();
+            }
+        });
+    }
+    // vector k's pages are resident (and the next AHEAD are being touched)
+    void ensure(int k) {
+        std::unique_lock<std::mutex> l(mu);
+        want = std::max(want, std::min(n_vec, k + 1 + AHEAD));
+        cv.notify_all();
+        cv.wait(l, [&]() { return touched > k; });
+    }
     // queue the copy of device vector k (made on stream s) to host slot k
     cudaError_t save(int k, const void* dev, size_t bytes, cudaStream_t s) {
-        touch(k);
+        ensure(k);
         cudaError_t e = cudaEventRecord(made[k & 3], s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, made[k & 3], 0);
         if (e == cudaSuccess) {
@@ -680,7 +724,7 @@ struct HostKrylov {
         if (e == cudaSuccess) e = cudaEventRecord(copied[k & 3], copy);
         return e;
     }
-    // first-touch the pages of vector k (parallel; the copy engine then writes resident pages)
+    // first-touch the pages of vector k (parallel; the copy kernel then writes resident pages)
     void touch(int k) const {
         const int nth = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
         const size_t per = (vec_bytes + nth - 1) / nth;
@@ -747,6 +791,7 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
                            -1, 0);
             if (p == MAP_FAILED) return fail(ED_ERR_NOMEM, "host range for %d Lanczos vectors", max_it + 1);
             hk.base = p;
+            hk.start(max_it + 1);
             ED_CUDA(cudaStreamCreateWithFlags(&hk.copy, cudaStreamNonBlocking));
             for (int i = 0; i < 4; ++i) {
                 ED_CUDA(cudaEventCreateWithFlags(&hk.made[i], cudaEventDisableTiming));
