@@ -253,7 +253,7 @@ def lanczos_pair(pkg, torch, H, real, D, stream, store_for, hx_fp64_s=None):
     run is the thesis's plain three-term recursion (the ground energy needs no
     stored vectors); the mixed run needs its Ritz vector for the FP64 Rayleigh
     quotient and keeps its Lanczos vectors in host memory (NVLink-C2C) instead of
-    running a second pass.  With hx_fp64_s (the stored FP64 H.x time measured
+    running a second pass, or on the device where they fit.  With hx_fp64_s (the stored FP64 H.x time measured
     beside it) the FP64 run's time outside H.x is reported per step against the
     HBM roofline of the plain recursion's vector algebra: per step, dot_step
     reads v_n and w, axpy_norm_step reads w, v_n, v_(n-1) and writes w, scale_by
@@ -262,14 +262,20 @@ def lanczos_pair(pkg, torch, H, real, D, stream, store_for, hx_fp64_s=None):
     for name, dt, refine in (("fp64", pkg.ED_F64 if real else pkg.ED_C128, False),
                              ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
         store_s = store_for(dt)
+        # the mixed run's plain-recursion vectors (up to 301 of them) stay on the
+        # device when they fit half the free memory, else they go to host memory
+        free, _ = torch.cuda.mem_get_info()
+        keep = 0 if not refine else (2 if 301 * D * (4 if real else 8) <= 0.5 * free else 1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=300, dtype=dt, reorth=False, refine=refine,
-                            raise_on_nonconv=False, stream=stream, host_vectors=refine)
+                            raise_on_nonconv=False, stream=stream, host_vectors=keep)
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         lz[name] = {"seconds": t + store_s, "lanczos_seconds": t, "store_seconds": store_s, "E0": float(ev[0]),
-                    "iters": rep.iters, "reorth": False, "host_vectors": refine, "max_iter": 300,
+                    "iters": rep.iters, "reorth": False,
+                    "lanczos_vectors": {0: "second pass or none", 1: "host memory", 2: "device memory"}[keep],
+                    "max_iter": 300,
                     "converged": bool(rep.converged), "ritz": rep.ritz[0], "n_apply": rep.n_apply}
     if hx_fp64_s:
         f = lz["fp64"]
@@ -399,7 +405,8 @@ def batching_measurement(pkg, torch, stream):
     against one batched Lanczos run over all sectors (every step one persistent
     H.x launch for all sectors, the step replayed as a CUDA graph), with one
     vector per sector (plain recursion or full reorthogonalisation) and with a
-    block of 8 seeded Gaussian vectors."""
+    block of 8 seeded Gaussian vectors; FP64 vectors, and FP32 vectors (FP32
+    block Gram-Schmidt, FP64 refinement: keys ending in _fp32)."""
     from edinputs import configs as EC
     probs = EC.triangular24_sectors()
     bases = [pkg.Basis(p.sector, stream=stream) for p in probs]
@@ -425,22 +432,25 @@ def batching_measurement(pkg, torch, stream):
     out = {"workload": "triangular 24 sites, all 36 (k, rho_k) sectors, J2=0.125, Sz=0",
            "total_dim": int(batch.total), "store_s": t_store, "hx_path": "stored structure of every sector",
            "sequential_s": t_seq, "E0_min": min(seq)}
-    for blk, reorth in ((1, False), (1, True), (8, True)):
-        x = torch.zeros(blk * batch.total, dtype=torch.complex128, device=dev)
+    for blk, reorth, fp32 in ((1, False, False), (1, True, False), (8, True, False), (1, True, True),
+                              (8, True, True)):
+        tdt, edt = (torch.complex64, pkg.ED_C64) if fp32 else (torch.complex128, pkg.ED_C128)
+        x = torch.zeros(blk * batch.total, dtype=tdt, device=dev)
         waves = batch.autotune(x, torch.empty_like(x), nvec=blk)
         del x
         max_it = 300 if blk == 1 else 80
         if blk == 1:  # warm-up run (the block-8 run is long enough to carry its own set-up)
             batch.lanczos(block=blk, n_eig=1, tol=1e-10, max_iter=max_it, seed=3, use_graph=True,
-                          raise_on_nonconv=False, reorth=reorth)
+                          raise_on_nonconv=False, reorth=reorth, dtype=edt)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, rep = batch.lanczos(block=blk, n_eig=1, tol=1e-10, max_iter=max_it, seed=3, use_graph=True,
-                                raise_on_nonconv=False, reorth=reorth)
+                                raise_on_nonconv=False, reorth=reorth, dtype=edt)
         torch.cuda.synchronize()
         t_bat = time.perf_counter() - t0
         diff = max(abs(float(ev[s, 0]) - seq[s]) for s in range(len(hs)))
-        out[f"block{blk}_{'reorth' if reorth else 'plain'}"] = {
+        key = f"block{blk}_{'reorth' if reorth else 'plain'}" + ("_fp32" if fp32 else "")
+        out[key] = {
             "batched_graph_s": t_bat, "speedup_vs_sequential": t_seq / t_bat, "iters": rep.iters,
             "step_seconds": rep.step_seconds, "converged_sectors": rep.converged_sectors,
             "max_abs_E0_diff": diff, "autotuned_waves": waves}

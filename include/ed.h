@@ -412,13 +412,14 @@ typedef struct {
                               Ritz vectors in FP64 get one FP64 H.x and their Rayleigh quotients; if
                               r^2/gap misses tol, at most this many FP64 Lanczos steps from their sum */
     int32_t check_every;   /* T-matrix eigensolve every this many steps (>= 1) */
-    int32_t host_vectors;  /* plain recursion only (reorth = 0): 1 = keep every Lanczos vector in host
-                              (system) memory as it is made, on a second stream, and form the Ritz vectors
-                              (evecs, and the mixed refinement's start) from there instead of by a second
-                              pass of iters H.x.  Needs a device that reads pageable host memory (e.g. over
-                              NVLink-C2C); elsewhere the second pass is used.  Host memory: (iters + 1)
-                              vectors of the dtype, reserved for max_iter + 1 and released on return.
-                              0 = second pass */
+    int32_t host_vectors;  /* plain recursion only (reorth = 0), where the Ritz vectors are needed:
+                              1 = keep every Lanczos vector in host (system) memory as it is made, on a
+                              second stream, and form the Ritz vectors (evecs, and the mixed refinement's
+                              start) from there instead of by a second pass of iters H.x.  Needs a device
+                              that reads pageable host memory (e.g. over NVLink-C2C); elsewhere the second
+                              pass is used.  Host memory: (iters + 1) vectors of the dtype, reserved for
+                              max_iter + 1 and released on return.  2 = keep them in device memory
+                              ((max_iter + 1) vectors of the dtype from the allocator).  0 = second pass */
 } ed_lanczos_opts;
 
 typedef struct {
@@ -536,12 +537,17 @@ ed_status ed_batch_autotune(ed_batch* batch, ed_dtype dtype, const void* x, void
 void ed_batch_free(ed_batch* batch);
 
 typedef struct {
-    ed_dtype dtype;        /* ED_F64 (all sectors real) or ED_C128 */
+    ed_dtype dtype;        /* ED_F64 (all sectors real) or ED_C128; or FP32 vectors, ED_F32 (all sectors
+                              real) or ED_C64, which need reorth = 1 and n_eig <= 8: the block
+                              Gram-Schmidt then runs in FP32 arithmetic (sums across row tiles and the
+                              b x b matrices in FP64), a sector stops when its values settle to tol or to
+                              the FP32 noise of T (8 eps_32 |T|), and the values are refined in FP64 */
     int32_t block;         /* right-hand sides per sector, 1..8 */
     int32_t n_eig;         /* lowest eigenvalues per sector */
     double tol;            /* convergence: each eigenvalue changed by at most tol/10 (relative) since the
-                              previous check, on two checks in a row; with block = 1 also the Ritz
-                              residual bound r = beta |s_last| within min(r, r^2/gap) <= tol (relative) */
+                              previous check, on two checks in a row, and its Ritz residual bound r
+                              (beta |s_last| for block = 1, |B_last z_last| for a Ritz vector z of the
+                              block T) within min(r, r^2/gap) <= tol (relative) */
     int32_t max_iter;      /* block steps at most (2..400) */
     uint64_t seed;         /* Gaussian start blocks from keyed SplitMix64 of (seed, column, state) */
     int32_t use_graph;     /* 1: capture one step (all kernels, all sectors) as a CUDA graph and replay it */
@@ -555,7 +561,8 @@ typedef struct {
 
 typedef struct {
     int32_t iters;             /* block steps taken */
-    int32_t converged_sectors; /* sectors whose n_eig values were steady for two checks */
+    int32_t converged_sectors; /* sectors whose n_eig values were steady for two checks (FP32
+                                  vectors: whose refined values are certified) */
     int32_t krylov_dim;        /* iters * block */
     int32_t used_graph;
     double seconds;            /* wall time of the call */
@@ -572,9 +579,22 @@ typedef struct {
  * products in FP64 with a fixed reduction order.  evals: HOST [n][n_eig]
  * (sector-major), lowest eigenvalues of each sector's block tridiagonal T
  * (degenerate eigenvalues appear with their multiplicity up to the block size).
+ * With FP32 vectors the values are then refined as ed_lanczos refines its
+ * mixed-precision run: per sector the Ritz vectors of the n_eig lowest values
+ * of T (inverse iteration on the band T) are formed in FP64 from the FP32
+ * blocks, one FP64 batched H.x is applied to all of them, and Rayleigh-Ritz
+ * on their span (which resolves degenerate copies) gives the returned values
+ * E and vectors y.  A sector counts as converged when every residual
+ * r = |Hy - E y| / |y| satisfies r <= tol |E| or r^2 / gap <= tol |E| (gap:
+ * the distance from E to the nearest Ritz value of T of another level, less r,
+ * values within max(10 r, 1e-6 |E|) of E counting as copies of its own level;
+ * the Rayleigh quotient's error is at most r^2 / gap).  Sectors not certified
+ * this way (a close next level) continue in FP64: block Lanczos from their
+ * refined vectors, with only those sectors iterating (at most 60 steps).
  * Workspace from the batch's allocator (or cudaMalloc), released before
- * return.  Synchronous (uses an internal stream).  ED_ERR_NOT_CONVERGED if
- * some sector did not settle within max_iter (values still written). */
+ * return.  Synchronous (uses an internal stream).
+ * ED_ERR_NOT_CONVERGED if some sector did not settle within max_iter, or (FP32
+ * vectors) its refined values are not certified (values still written). */
 ed_status ed_lanczos_batch(const ed_batch* batch, const ed_block_lanczos_opts* opts, double* evals,
                            ed_block_lanczos_report* report, ed_stream stream);
 

@@ -53,17 +53,35 @@ namespace ed {
 static const int TILE = 4096;  // rows per reduction tile
 static const int MAXB = 8;
 
+// Vector kinds of block Lanczos: T is the stored element, A the complex type
+// of the elementwise arithmetic (FP32 for FP32 vectors, so that the block
+// Gram-Schmidt runs on the FP32 pipes; sums across tiles and the b x b
+// matrices stay FP64).
 template <int K> struct BV;
-template <> struct BV<0> { using T = double; static constexpr bool cplx = false; };
-template <> struct BV<2> { using T = double2; static constexpr bool cplx = true; };
+template <> struct BV<0> { using T = double; using A = double2; static constexpr bool cplx = false, single = false; };
+template <> struct BV<1> { using T = float; using A = float2; static constexpr bool cplx = false, single = true; };
+template <> struct BV<2> { using T = double2; using A = double2; static constexpr bool cplx = true, single = false; };
+template <> struct BV<3> { using T = float2; using A = float2; static constexpr bool cplx = true, single = true; };
 
 __device__ __forceinline__ double2 c_ld(const double& v) { return make_double2(v, 0.0); }
 __device__ __forceinline__ double2 c_ld(const double2& v) { return v; }
+__device__ __forceinline__ float2 c_ld(const float& v) { return make_float2(v, 0.f); }
+__device__ __forceinline__ float2 c_ld(const float2& v) { return v; }
 __device__ __forceinline__ void c_st(double& d, double2 v) { d = v.x; }
 __device__ __forceinline__ void c_st(double2& d, double2 v) { d = v; }
+__device__ __forceinline__ void c_st(float& d, float2 v) { d = v.x; }
+__device__ __forceinline__ void c_st(float2& d, float2 v) { d = v; }
+__device__ __forceinline__ void c_st(float& d, double2 v) { d = (float)v.x; }
+__device__ __forceinline__ void c_st(float2& d, double2 v) { d = make_float2((float)v.x, (float)v.y); }
+__device__ __forceinline__ double2 to_d2(double2 v) { return v; }
+__device__ __forceinline__ double2 to_d2(float2 v) { return make_double2(v.x, v.y); }
 __device__ __forceinline__ double2 c_mul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ double2 c_conjmul(double2 a, double2 b) {  // conj(a) b
     return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float2 c_mul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 c_conjmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
 }
 
 __device__ __forceinline__ int sector_of(const int64_t* row_off, int n, int64_t r) {
@@ -134,18 +152,19 @@ __global__ void __launch_bounds__(256) bl_gram(const typename BV<K>::T* X, int64
     const int lanes = 256 / bb;
     const int t = threadIdx.x;
     __shared__ double2 red[256];
-    double2 acc = make_double2(0.0, 0.0);
+    using A = typename BV<K>::A;
+    A acc{0, 0};
     if (t < lanes * bb) {
         const int a = (t / b) % b, c = t % b, l = t / bb;
         const typename BV<K>::T* xa = X + (int64_t)j * xs + base + (int64_t)a * D;
         const typename BV<K>::T* yc = Y + base + (int64_t)c * D;
         for (int64_t i = i0 + l; i < i1; i += lanes) {
-            const double2 p = c_conjmul(c_ld(xa[i]), c_ld(yc[i]));
+            const A p = c_conjmul(c_ld(xa[i]), c_ld(yc[i]));
             acc.x += p.x;
             acc.y += p.y;
         }
     }
-    red[t] = acc;
+    red[t] = to_d2(acc);  // FP64 from here on
     __syncthreads();
     if (t < bb) {
         double2 sum = make_double2(0.0, 0.0);
@@ -157,9 +176,10 @@ __global__ void __launch_bounds__(256) bl_gram(const typename BV<K>::T* X, int64
     }
 }
 
-// C[s][j][a][c] = sum over the tiles of sector s (fixed order)
+// C[s][j][a][c] = sum over the tiles of sector s (fixed order); Cf (if not
+// null) receives the same values in FP32 for the FP32 update
 __global__ void bl_reduce(const double2* partial, const int* tile_first, int n, int b, int n_tiles, const int* jmax,
-                          int jcap, double2* C, int local) {
+                          int jcap, double2* C, int local, float2* Cf = nullptr) {
     const int s = blockIdx.x;
     const int bb = b * b;
     const int jm = jmax ? *jmax : 0;
@@ -173,6 +193,7 @@ __global__ void bl_reduce(const double2* partial, const int* tile_first, int n, 
             sum.y += v.y;
         }
         C[((int64_t)s * jcap + j) * bb + ac] = sum;
+        if (Cf) Cf[((int64_t)s * jcap + j) * bb + ac] = make_float2((float)sum.x, (float)sum.y);
     }
 }
 
@@ -180,7 +201,8 @@ __global__ void bl_reduce(const double2* partial, const int* tile_first, int n, 
 template <int K>
 __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int64_t xs, const int* jmax,
                           const double2* C, int jcap, const int64_t* row_off, int n, int b, int local,
-                          const int* active) {
+                          const int* active, const float2* Cf = nullptr) {
+    using A = typename BV<K>::A;
     const int64_t total = row_off[n];
     const int jm = *jmax;
     const int j0 = local ? max(0, jm - 1) : 0;
@@ -191,14 +213,17 @@ __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int6
         const int64_t i = r - row_off[s];
         const int64_t D = row_off[s + 1] - row_off[s];
         const int64_t base = (int64_t)b * row_off[s];
-        double2 w[MAXB];
+        A w[MAXB];
         for (int c = 0; c < b; ++c) w[c] = c_ld(W[base + (int64_t)c * D + i]);
         for (int j = j0; j <= jm; ++j) {
-            const double2* Cj = C + ((int64_t)s * jcap + j) * bb;
+            const int64_t cj = ((int64_t)s * jcap + j) * bb;
             for (int a = 0; a < b; ++a) {
-                const double2 x = c_ld(X[(int64_t)j * xs + base + (int64_t)a * D + i]);
+                const A x = c_ld(X[(int64_t)j * xs + base + (int64_t)a * D + i]);
                 for (int c = 0; c < b; ++c) {
-                    const double2 p = c_mul(x, Cj[a * b + c]);
+                    A cv;
+                    if constexpr (BV<K>::single) cv = Cf[cj + a * b + c];
+                    else cv = C[cj + a * b + c];
+                    const A p = c_mul(x, cv);
                     w[c].x -= p.x;
                     w[c].y -= p.y;
                 }
@@ -212,7 +237,7 @@ __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int6
 // accumulate Bacc = R * Bacc (Bacc starts as the identity).  A column whose
 // pivot collapses is dropped (R^{-1} column zero).
 __global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv, double2* Bacc, int first_pass,
-                        const int* active) {
+                        const int* active, float2* Rinvf = nullptr) {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= n || !active[s]) return;
     const int bb = b * b;
@@ -260,6 +285,7 @@ __global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv,
     for (int r = 0; r < b; ++r)
         for (int c = 0; c < b; ++c) {
             ri[r * b + c] = Ri[r][c];
+            if (Rinvf) Rinvf[(int64_t)s * bb + r * b + c] = make_float2((float)Ri[r][c].x, (float)Ri[r][c].y);
             double2 v = make_double2(0, 0);
             for (int k = 0; k < b; ++k) {
                 const double2 prev = first_pass ? make_double2(k == c ? 1.0 : 0.0, 0.0) : ba[k * b + c];
@@ -276,7 +302,9 @@ __global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv,
 // Out[c][i] = sum_a W[a][i] Rinv[s][a][c]; Out may be W + (*kout)*os (device index) or W itself
 template <int K>
 __global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int64_t os, const int* kout, int kadd,
-                         const double2* Rinv, const int64_t* row_off, int n, int b, const int* active) {
+                         const double2* Rinv, const int64_t* row_off, int n, int b, const int* active,
+                         const float2* Rinvf = nullptr) {
+    using A = typename BV<K>::A;
     const int64_t total = row_off[n];
     typename BV<K>::T* out = Out + (kout ? (int64_t)(*kout + kadd) * os : 0);
     const int bb = b * b;
@@ -286,13 +314,15 @@ __global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int
         const int64_t i = r - row_off[s];
         const int64_t D = row_off[s + 1] - row_off[s];
         const int64_t base = (int64_t)b * row_off[s];
-        double2 w[MAXB];
+        A w[MAXB];
         for (int a = 0; a < b; ++a) w[a] = c_ld(W[base + (int64_t)a * D + i]);
-        const double2* R = Rinv + (int64_t)s * bb;
         for (int c = 0; c < b; ++c) {
-            double2 v = make_double2(0, 0);
+            A v{0, 0};
             for (int a = 0; a < b; ++a) {
-                const double2 p = c_mul(w[a], R[a * b + c]);
+                A rv;
+                if constexpr (BV<K>::single) rv = Rinvf[(int64_t)s * bb + a * b + c];
+                else rv = Rinv[(int64_t)s * bb + a * b + c];
+                const A p = c_mul(w[a], rv);
                 v.x += p.x;
                 v.y += p.y;
             }
@@ -319,6 +349,83 @@ __global__ void bl_save(const double2* C1, const double2* C2, const double2* Bac
 }
 
 __global__ void bl_set_int(int* p, int v) { *p = v; }
+
+// Refinement of FP32 block Lanczos: Ritz vectors in FP64,
+// Y[e][i] = sum over j < its[s] and a < b of V_j[a][i] Z[s][e][j b + a]
+// (sector s's ne columns start at ne * row_off[s], column e at + e D).
+template <int KV, int KO>
+__global__ void bl_combine(typename BV<KO>::T* Y, int ne, const typename BV<KV>::T* V, int64_t bs, const double2* Z,
+                           int zcap, const int* its, const int64_t* row_off, int n, int b) {
+    const int64_t total = row_off[n];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sector_of(row_off, n, r);
+        const int64_t i = r - row_off[s];
+        const int64_t D = row_off[s + 1] - row_off[s];
+        const int64_t base = (int64_t)b * row_off[s];
+        double2 acc[MAXB];
+        for (int e = 0; e < ne; ++e) acc[e] = make_double2(0, 0);
+        const int it = its[s];
+        for (int j = 0; j < it; ++j)
+            for (int a = 0; a < b; ++a) {
+                const double2 x = to_d2(c_ld(V[(int64_t)j * bs + base + (int64_t)a * D + i]));
+                for (int e = 0; e < ne; ++e) {
+                    const double2 p = c_mul(x, Z[((int64_t)s * ne + e) * zcap + j * b + a]);
+                    acc[e].x += p.x;
+                    acc[e].y += p.y;
+                }
+            }
+        const int64_t yb = (int64_t)ne * row_off[s];
+        for (int e = 0; e < ne; ++e) c_st(Y[yb + (int64_t)e * D + i], acc[e]);
+    }
+}
+
+// Y[.][i] <- Y[.][i] C[s] and HY[.][i] <- HY[.][i] C[s] (C[s]: ne x ne, [a][e]),
+// in place row by row (the Ritz vectors of the Rayleigh-Ritz step)
+template <int KO>
+__global__ void bl_rotate(typename BV<KO>::T* Y, typename BV<KO>::T* HY, const double2* C, int ne,
+                          const int64_t* row_off, int n) {
+    const int64_t total = row_off[n];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sector_of(row_off, n, r);
+        const int64_t i = r - row_off[s];
+        const int64_t D = row_off[s + 1] - row_off[s];
+        const int64_t yb = (int64_t)ne * row_off[s];
+        const double2* Cs = C + (int64_t)s * ne * ne;
+        for (int w = 0; w < 2; ++w) {
+            typename BV<KO>::T* X = w == 0 ? Y : HY;
+            double2 in[MAXB], out[MAXB];
+            for (int a = 0; a < ne; ++a) in[a] = c_ld(X[yb + (int64_t)a * D + i]);
+            for (int e = 0; e < ne; ++e) {
+                out[e] = make_double2(0, 0);
+                for (int a = 0; a < ne; ++a) {
+                    const double2 p = c_mul(in[a], Cs[a * ne + e]);
+                    out[e].x += p.x;
+                    out[e].y += p.y;
+                }
+            }
+            for (int e = 0; e < ne; ++e) c_st(X[yb + (int64_t)e * D + i], out[e]);
+        }
+    }
+}
+
+// R[e][i] = HY[e][i] - E[s][e] Y[e][i], in place on HY (FP64 kinds)
+template <int KO>
+__global__ void bl_resid(typename BV<KO>::T* HY, const typename BV<KO>::T* Y, const double* E, int ne,
+                         const int64_t* row_off, int n) {
+    const int64_t total = row_off[n];
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < total; r += (int64_t)gridDim.x * blockDim.x) {
+        const int s = sector_of(row_off, n, r);
+        const int64_t i = r - row_off[s];
+        const int64_t D = row_off[s + 1] - row_off[s];
+        const int64_t yb = (int64_t)ne * row_off[s];
+        for (int e = 0; e < ne; ++e) {
+            const int64_t o = yb + (int64_t)e * D + i;
+            const double2 h = c_ld(HY[o]), y = c_ld(Y[o]);
+            const double en = E[s * ne + e];
+            c_st(HY[o], make_double2(h.x - en * y.x, h.y - en * y.y));
+        }
+    }
+}
 
 // ------------------------------------------------------------------ host: banded eigenvalues
 using cd = std::complex<double>;
@@ -376,6 +483,147 @@ static std::vector<double> band_lowest(const Band& T, int m) {
         out.push_back(0.5 * (a + b2));
     }
     return out;
+}
+
+// max row sum of |T| (a bound on its spectral radius)
+static double band_norm(const Band& T) {
+    double tn = 0.0;
+    for (int i = 0; i < T.n; ++i) {
+        double r = 0.0;
+        for (int k = 0; k <= T.bw && k <= i; ++k) r += std::abs(T.get(i, k));
+        for (int k = 1; k <= T.bw && i + k < T.n; ++k) r += std::abs(T.get(i + k, k));
+        tn = std::max(tn, r);
+    }
+    return tn;
+}
+
+// Eigenvector of the Hermitian band matrix T for its eigenvalue lam, by
+// inverse iteration: (T - lam I) z_new = z, solved by Gaussian elimination
+// with partial pivoting inside the band (row interchanges make the upper
+// bandwidth 2 bw; the multipliers of step k stay in column k, as the solve
+// applies interchange k before elimination k).  Three iterations from a
+// fixed start; each iterate is orthogonalised against `prev` (vectors of
+// lower eigenvalues of the same T, which matters for close pairs).
+static std::vector<cd> band_vector(const Band& T, double lam, const std::vector<std::vector<cd>>& prev) {
+    const int n = T.n, bw = T.bw, w = 3 * bw + 1;  // row i holds columns i - bw .. i + 2 bw
+    double tn = 0.0;
+    for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+        for (int k = 0; k <= bw && k <= i; ++k) r += std::abs(T.get(i, k));
+        for (int k = 1; k <= bw && i + k < n; ++k) r += std::abs(T.get(i + k, k));
+        tn = std::max(tn, r);
+    }
+    const double tiny = 1e-14 * std::max(tn, 1e-300);
+    std::vector<cd> M((size_t)n * w, cd(0));
+    auto at = [&](int i, int j) -> cd& { return M[(size_t)i * w + (j - i + bw)]; };
+    for (int i = 0; i < n; ++i)
+        for (int j = std::max(0, i - bw); j <= std::min(n - 1, i + bw); ++j)
+            at(i, j) = (i >= j ? T.get(i, i - j) : std::conj(T.get(j, j - i))) - (i == j ? cd(lam) : cd(0));
+    std::vector<int> piv(n);
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i)
+            if (std::abs(at(i, k)) > std::abs(at(p, k))) p = i;
+        piv[k] = p;
+        const int jend = std::min(n - 1, k + 2 * bw);
+        if (p != k)
+            for (int j = k; j <= jend; ++j) std::swap(at(k, j), at(p, j));
+        if (std::abs(at(k, k)) < tiny) at(k, k) = cd(tiny);
+        for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i) {
+            const cd f = at(i, k) / at(k, k);
+            at(i, k) = f;
+            for (int j = k + 1; j <= jend; ++j) at(i, j) -= f * at(k, j);
+        }
+    }
+    std::vector<cd> z(n);
+    for (int i = 0; i < n; ++i) z[i] = cd(1.0 + 0.5 * std::sin(1.0 + 0.77 * i), 0.25 * std::cos(0.3 + 1.3 * i));
+    for (int iter = 0; iter < 3; ++iter) {
+        for (int k = 0; k < n; ++k) {
+            std::swap(z[k], z[piv[k]]);
+            for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i) z[i] -= at(i, k) * z[k];
+        }
+        for (int i = n - 1; i >= 0; --i) {
+            cd v = z[i];
+            for (int j = i + 1; j <= std::min(n - 1, i + 2 * bw); ++j) v -= at(i, j) * z[j];
+            z[i] = v / at(i, i);
+        }
+        for (const auto& q : prev) {
+            cd d = 0;
+            for (int i = 0; i < n; ++i) d += std::conj(q[i]) * z[i];
+            for (int i = 0; i < n; ++i) z[i] -= d * q[i];
+        }
+        double nr = 0.0;
+        for (int i = 0; i < n; ++i) nr += std::norm(z[i]);
+        nr = std::sqrt(nr);
+        if (!(nr > 0.0)) break;
+        for (int i = 0; i < n; ++i) z[i] /= nr;
+    }
+    return z;
+}
+
+// Rayleigh-Ritz on an ne-dimensional subspace spanned by the columns of Y:
+// M = Y^H H Y and G = Y^H Y (row-major ne x ne).  With G = L L^H (Cholesky)
+// the pencil (M, G) becomes the Hermitian A = L^-1 M L^-H; its eigenpairs
+// (A v = E v; bisection and inverse iteration on A as a band of width ne - 1)
+// give C = L^-H V, so that Y C is orthonormal and (Y C)^H H (Y C) = diag(E).
+// False if G is not positive definite.
+static bool small_ritz(int ne, const std::vector<cd>& M, const std::vector<cd>& G, std::vector<double>& E,
+                       std::vector<cd>& C) {
+    std::vector<cd> L((size_t)ne * ne, cd(0));
+    for (int j = 0; j < ne; ++j) {
+        double d = G[(size_t)j * ne + j].real();
+        for (int k = 0; k < j; ++k) d -= std::norm(L[(size_t)j * ne + k]);
+        if (!(d > 0.0)) return false;
+        L[(size_t)j * ne + j] = std::sqrt(d);
+        for (int i = j + 1; i < ne; ++i) {
+            cd v = G[(size_t)i * ne + j];
+            for (int k = 0; k < j; ++k) v -= L[(size_t)i * ne + k] * std::conj(L[(size_t)j * ne + k]);
+            L[(size_t)i * ne + j] = v / L[(size_t)j * ne + j];
+        }
+    }
+    auto fwd = [&](std::vector<cd>& x) {  // x <- L^-1 x
+        for (int i = 0; i < ne; ++i) {
+            cd v = x[i];
+            for (int k = 0; k < i; ++k) v -= L[(size_t)i * ne + k] * x[k];
+            x[i] = v / L[(size_t)i * ne + i];
+        }
+    };
+    // X = L^-1 M (column by column), A = (L^-1 X^H)^H
+    std::vector<cd> X((size_t)ne * ne), A((size_t)ne * ne), col(ne);
+    for (int c = 0; c < ne; ++c) {
+        for (int i = 0; i < ne; ++i) col[i] = M[(size_t)i * ne + c];
+        fwd(col);
+        for (int i = 0; i < ne; ++i) X[(size_t)i * ne + c] = col[i];
+    }
+    for (int c = 0; c < ne; ++c) {
+        for (int i = 0; i < ne; ++i) col[i] = std::conj(X[(size_t)c * ne + i]);  // column c of X^H
+        fwd(col);
+        for (int i = 0; i < ne; ++i) A[(size_t)c * ne + i] = std::conj(col[i]);
+    }
+    Band T;
+    T.n = ne;
+    T.bw = ne - 1;
+    T.L.assign((size_t)ne * ne, cd(0));
+    for (int i = 0; i < ne; ++i)
+        for (int k = 0; k <= i; ++k)
+            T.at(i, k) = 0.5 * (A[(size_t)i * ne + (i - k)] + std::conj(A[(size_t)(i - k) * ne + i]));
+    E = band_lowest(T, ne);
+    if ((int)E.size() != ne) return false;
+    std::vector<std::vector<cd>> vs;
+    C.assign((size_t)ne * ne, cd(0));
+    for (int e = 0; e < ne; ++e) {
+        std::vector<cd> v = band_vector(T, E[e], vs);
+        // c = L^-H v: back substitution with the upper-triangular L^H
+        std::vector<cd> c = v;
+        for (int i = ne - 1; i >= 0; --i) {
+            cd w = c[i];
+            for (int k = i + 1; k < ne; ++k) w -= std::conj(L[(size_t)k * ne + i]) * c[k];
+            c[i] = w / std::conj(L[(size_t)i * ne + i]);
+        }
+        for (int a = 0; a < ne; ++a) C[(size_t)a * ne + e] = c[a];
+        vs.push_back(std::move(v));
+    }
+    return true;
 }
 
 // ------------------------------------------------------------------ batch construction and apply
@@ -585,9 +833,14 @@ void ed_batch_free(ed_batch* B) {
 
 namespace ed {
 
+// start (optional): DEVICE start blocks of the vector kind (b columns per
+// sector, the batch layout) instead of Gaussian ones; only (optional): the
+// sectors that iterate (others keep their slots untouched); conv (optional):
+// per sector whether it converged.
 template <int K>
 static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o, double* evals,
-                               ed_block_lanczos_report* rep, cudaStream_t user_stream) {
+                               ed_block_lanczos_report* rep, cudaStream_t user_stream, const void* start = nullptr,
+                               const std::vector<int>* only = nullptr, std::vector<char>* conv = nullptr) {
     using T = typename BV<K>::T;
     auto t0 = std::chrono::steady_clock::now();
     const int n = B->n, b = o->block, kcap = o->max_iter + 1, nt = B->n_tiles;
@@ -625,7 +878,20 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     int* active = (int*)get((size_t)n * 4);  // 1 while a sector iterates; converged sectors drop out
     if (!V || !W || !part || !C1 || !C2 || !G || !Rinv || !Bacc || !Ahist || !Bhist || !dk || !tile_first || !active)
         return fail(ED_ERR_NOMEM, "block Lanczos workspace");
+    // FP32 vectors: FP32 copies of the coefficients for the elementwise updates
+    constexpr bool single = BV<K>::single;
+    float2* C1f = nullptr;
+    float2* C2f = nullptr;
+    float2* Rinvf = nullptr;
+    if (single) {
+        C1f = (float2*)get((size_t)n * kcap * bb * sizeof(float2));
+        C2f = (float2*)get((size_t)n * kcap * bb * sizeof(float2));
+        Rinvf = (float2*)get((size_t)n * bb * sizeof(float2));
+        if (!C1f || !C2f || !Rinvf) return fail(ED_ERR_NOMEM, "block Lanczos workspace");
+    }
     std::vector<int> act_h(n, 1);
+    if (only) act_h = *only;
+    const int n_run = (int)std::count(act_h.begin(), act_h.end(), 1);
     ED_CUDA(cudaMemcpy(active, act_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     {
         std::vector<int> tf(n + 1, 0);
@@ -651,14 +917,15 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     const int64_t* tiles = (const int64_t*)B->d_tiles.p;
     const HxArgs* desc = (const HxArgs*)B->d_desc.p;
     // start block V_0 = orth(X), via CholQR2 on the Gaussian block
-    bl_init<K><<<g, 256, 0, s>>>(W, desc, ro, n, b, o->seed, B->w8 ? 8 : 4);
+    if (start) ED_CUDA(cudaMemcpyAsync(W, start, (size_t)bs * sizeof(T), cudaMemcpyDeviceToDevice, s));
+    else bl_init<K><<<g, 256, 0, s>>>(W, desc, ro, n, b, o->seed, B->w8 ? 8 : 4);
     auto cholqr = [&](T* src, T* dst, int64_t dst_os, const int* kout, int kadd) {
         for (int pass = 0; pass < 2; ++pass) {
             bl_gram<K><<<dim3(nt, 1), 256, 0, s>>>(src, 0, nullptr, src, tiles, ro, b, part, nt, 0, active);
             bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, nullptr, kcap, G, 0);
-            bl_chol<<<(n + 63) / 64, 64, 0, s>>>(G, kcap, n, b, Rinv, Bacc, pass == 0, active);
+            bl_chol<<<(n + 63) / 64, 64, 0, s>>>(G, kcap, n, b, Rinv, Bacc, pass == 0, active, Rinvf);
             bl_scale<K><<<g, 256, 0, s>>>(src, pass == 0 ? src : dst, dst_os, pass == 0 ? nullptr : kout, kadd, Rinv,
-                                          ro, n, b, active);
+                                          ro, n, b, active, Rinvf);
         }
     };
     bl_set_int<<<1, 1, 0, s>>>(dk, 0);
@@ -681,10 +948,11 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         // orthogonality at half the FP64 cost of two full passes.
         for (int pass = 0; pass < 2; ++pass) {
             double2* Cp = pass == 0 ? C1 : C2;
+            float2* Cpf = pass == 0 ? C1f : C2f;
             const int win = (local || pass == 1) ? 1 : 0;
             bl_gram<K><<<dim3(nt, win ? 2 : kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt, win, active);
-            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp, win);
-            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, win, active);
+            bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp, win, Cpf);
+            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, win, active, Cpf);
         }
         cholqr(W, V, bs, dk, 1);  // V_{k+1} = W R^-1, B_k accumulated in Bacc
         bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
@@ -695,7 +963,9 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     {
         ed_status st = apply_batch_launch(L, s);
         if (st != ED_OK) return st;
-        bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b, local, active);
+        ED_CUDA(cudaMemsetAsync(C1, 0, (size_t)n * kcap * bb * sizeof(double2), s));
+        if (single) ED_CUDA(cudaMemsetAsync(C1f, 0, (size_t)n * kcap * bb * sizeof(float2), s));
+        bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b, local, active, C1f);
         bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
         bl_set_int<<<1, 1, 0, s>>>(dk, 0);
         ED_CUDA(cudaGetLastError());
@@ -728,6 +998,50 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     int iters = 0, conv_all = 0;
     double t_steps = 0;
     const int every = std::max(1, o->check_every);
+    std::vector<int> its_last(n, 0);  // Krylov blocks of each sector's last check
+    // Sector sct's T over its first `it` blocks (it*b square): diagonal blocks
+    // A_j (Hermitian part), block (j+1, j) = B_j, in band storage.  Columns of
+    // V_{j+1} that collapsed in the Cholesky QR (zero diagonal of B_j, a sector
+    // smaller than the Krylov space) are left out; pos maps the full index
+    // j b + a to T's row (-1 when left out).  Returns T's size.
+    auto build_T = [&](int sct, int it, Band& T, std::vector<int>& pos) -> int {
+        const int ntf = it * b;
+        std::vector<char> valid(ntf, 1);
+        double tn = 0.0;
+        for (int j = 0; j < it; ++j) {
+            const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
+            for (int r = 0; r < b; ++r) tn = std::max(tn, std::abs(cd(Aj[r * b + r].x, Aj[r * b + r].y)));
+        }
+        for (int j = 0; j + 1 < it; ++j) {
+            const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
+            for (int r = 0; r < b; ++r)
+                if (!(Bj[r * b + r].x > 1e-12 * std::max(tn, 1e-300))) valid[(j + 1) * b + r] = 0;
+        }
+        pos.assign(ntf, -1);
+        int nk2 = 0;
+        for (int q = 0; q < ntf; ++q)
+            if (valid[q]) pos[q] = nk2++;
+        T.n = nk2;
+        T.bw = 2 * b - 1;
+        T.L.assign((size_t)nk2 * (T.bw + 1), cd(0));
+        auto put = [&](int r, int c, cd v) {  // lower-triangle entry (r >= c) of the full index space
+            if (pos[r] < 0 || pos[c] < 0) return;
+            T.at(pos[r], pos[r] - pos[c]) = v;
+        };
+        for (int j = 0; j < it; ++j) {
+            const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
+            for (int r = 0; r < b; ++r)
+                for (int c = 0; c <= r; ++c)
+                    put(j * b + r, j * b + c,
+                        0.5 * (cd(Aj[r * b + c].x, Aj[r * b + c].y) + std::conj(cd(Aj[c * b + r].x, Aj[c * b + r].y))));
+            if (j + 1 < it) {
+                const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
+                for (int r = 0; r < b; ++r)
+                    for (int c = 0; c < b; ++c) put((j + 1) * b + r, j * b + c, cd(Bj[r * b + c].x, Bj[r * b + c].y));
+            }
+        }
+        return nk2;
+    };
     for (int k = 0; k + 1 < kcap; ++k) {
         auto ts = std::chrono::steady_clock::now();
         if (gexec) ED_CUDA(cudaGraphLaunch(gexec, s));
@@ -742,51 +1056,20 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         if ((k + 1) % every && !last) continue;
         ED_CUDA(cudaMemcpy(Ah.data(), Ahist, Ah.size() * sizeof(double2), cudaMemcpyDeviceToHost));
         ED_CUDA(cudaMemcpy(Bh.data(), Bhist, Bh.size() * sizeof(double2), cudaMemcpyDeviceToHost));
-        // T (iters*b square): diag blocks A_j, block (j+1, j) = B_j, in band
-        // storage.  Columns of V_{j+1} that collapsed in the Cholesky QR (zero
-        // diagonal of B_j, a sector smaller than the Krylov space) are left out.
         const int nt2 = iters * b;
         auto check_sector = [&](int sct) {
             if (!act_h[sct]) return;  // converged earlier: its values stay
-            std::vector<char> valid(nt2, 1);
-            double tn = 0.0;
-            for (int j = 0; j < iters; ++j) {
-                const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
-                for (int r = 0; r < b; ++r) tn = std::max(tn, std::abs(cd(Aj[r * b + r].x, Aj[r * b + r].y)));
-            }
-            for (int j = 0; j + 1 < iters; ++j) {
-                const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
-                for (int r = 0; r < b; ++r)
-                    if (!(Bj[r * b + r].x > 1e-12 * std::max(tn, 1e-300))) valid[(j + 1) * b + r] = 0;
-            }
-            std::vector<int> pos(nt2, -1);
-            int nk2 = 0;
-            for (int i = 0; i < nt2; ++i)
-                if (valid[i]) pos[i] = nk2++;
+            its_last[sct] = iters;
             Band T;
-            T.n = nk2;
-            T.bw = 2 * b - 1;
-            T.L.assign((size_t)nk2 * (T.bw + 1), cd(0));
-            auto put = [&](int r, int c, cd v) {  // lower-triangle entry (r >= c) of the full index space
-                if (pos[r] < 0 || pos[c] < 0) return;
-                T.at(pos[r], pos[r] - pos[c]) = v;
-            };
-            for (int j = 0; j < iters; ++j) {
-                const double2* Aj = &Ah[((size_t)sct * kcap + j) * bb];
-                for (int r = 0; r < b; ++r)
-                    for (int c = 0; c <= r; ++c)  // Hermitian part of A_j
-                        put(j * b + r, j * b + c,
-                            0.5 * (cd(Aj[r * b + c].x, Aj[r * b + c].y) + std::conj(cd(Aj[c * b + r].x, Aj[c * b + r].y))));
-                if (j + 1 < iters) {
-                    const double2* Bj = &Bh[((size_t)sct * kcap + j) * bb];
-                    for (int r = 0; r < b; ++r)
-                        for (int c = 0; c < b; ++c) put((j + 1) * b + r, j * b + c, cd(Bj[r * b + c].x, Bj[r * b + c].y));
-                }
-            }
+            std::vector<int> pos;
+            const int nk2 = build_T(sct, iters, T, pos);
+            // FP32 vectors: eigenvalue changes below the FP32 noise of T count as steady
+            const double floor32 = single ? 8.0 * 5.960464477539063e-08 * band_norm(T) : 0.0;
             // converged: every wanted value changed by at most tol/10 (relative)
-            // since the last check, on two checks in a row; with blocks of one
-            // also a small residual bound r = beta |s_last| of the Ritz pair
-            // (eigenvalue error at most min(r, r^2/gap)), as in ed_lanczos
+            // since the last check, on two checks in a row, and its Ritz pair
+            // has a small residual bound r (eigenvalue error at most
+            // min(r, r^2/gap)), as in ed_lanczos; FP32 vectors stop at their
+            // noise floor instead (the refinement below certifies the values)
             std::vector<double> lam, last;
             bool ok;
             if (b == 1) {
@@ -803,17 +1086,43 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
                     for (int q = 0; q < (int)lam.size(); ++q)
                         if (q != e) gap = std::min(gap, fabs(lam[q] - lam[e]));
                     const double rb = bh * fabs(last[e]);
-                    if (!(rb <= o->tol * sc || rb * rb <= o->tol * sc * gap)) ok = false;
+                    if (!(rb <= std::max(o->tol * sc, floor32) || rb * rb <= o->tol * sc * gap)) ok = false;
                 }
                 if ((int)lam.size() > n_eig) lam.resize(n_eig);
             } else {
-                lam = band_lowest(T, n_eig);
-                ok = (int)lam.size() == n_eig;
+                // blocks: the Ritz vector z of each value (inverse iteration on
+                // T) gives the residual |H y - lam y| = |B_last z_last| of
+                // y = V z, z_last the components in the last block
+                lam = band_lowest(T, n_eig + b);
+                ok = (int)lam.size() >= n_eig;
+                const double2* Bl = &Bh[((size_t)sct * kcap + iters - 1) * bb];
+                std::vector<std::vector<cd>> zs;
+                for (int e = 0; e < n_eig && ok; ++e) {
+                    std::vector<cd> z = band_vector(T, lam[e], zs);
+                    double rb = 0.0;
+                    for (int r = 0; r < b; ++r) {
+                        cd v = 0;
+                        for (int c = 0; c < b; ++c) {
+                            const int q = pos[(iters - 1) * b + c];
+                            if (q >= 0) v += cd(Bl[r * b + c].x, Bl[r * b + c].y) * z[q];
+                        }
+                        rb += std::norm(v);
+                    }
+                    rb = std::sqrt(rb);
+                    zs.push_back(std::move(z));
+                    const double sc = std::max(1.0, fabs(lam[e]));
+                    const double same = std::max(10.0 * rb, 1e-6 * sc);  // copies of the same level
+                    double gap = 1e300;
+                    for (double q : lam)
+                        if (fabs(q - lam[e]) > same) gap = std::min(gap, fabs(q - lam[e]));
+                    if (!(rb <= std::max(o->tol * sc, floor32) || rb * rb <= o->tol * sc * gap)) ok = false;
+                }
+                if ((int)lam.size() > n_eig) lam.resize(n_eig);
             }
             for (int e = 0; e < (int)lam.size(); ++e) {
                 cur[sct][e] = lam[e];
                 const double sc = std::max(1.0, fabs(lam[e]));
-                if (fabs(lam[e] - prev[sct][e]) > 0.1 * o->tol * sc) ok = false;
+                if (fabs(lam[e] - prev[sct][e]) > std::max(0.1 * o->tol * sc, floor32)) ok = false;
             }
             steady[sct] = ok ? steady[sct] + 1 : 0;
             prev[sct] = cur[sct];
@@ -832,16 +1141,175 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         int nconv = 0;
         bool changed = false;
         for (int sct = 0; sct < n; ++sct)
-            if (steady[sct] >= 2) {
+            if (steady[sct] >= 2 && (!only || (*only)[sct])) {
                 ++nconv;
                 if (act_h[sct]) {
                     act_h[sct] = 0;  // converged: later steps skip its rows
                     changed = true;
                 }
             }
-        if (changed && nconv < n) ED_CUDA(cudaMemcpy(active, act_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+        if (changed && nconv < n_run) ED_CUDA(cudaMemcpy(active, act_h.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
         conv_all = nconv;
-        if (nconv == n || last) break;
+        if (nconv == n_run || last) break;
+    }
+    std::vector<char> okv(n, 0);  // per sector: converged
+    for (int sct = 0; sct < n; ++sct) okv[sct] = steady[sct] >= 2 && (!only || (*only)[sct]);
+    if constexpr (single) {
+        // Refinement (as ed_lanczos's mixed path): per sector the Ritz vectors
+        // of its n_eig lowest values in FP64 from the FP32 blocks, one FP64 H.x
+        // of all of them in one batched launch, then Rayleigh-Ritz on their
+        // span (a block run holds degenerate copies, which one quotient per
+        // vector could not resolve) giving values E and vectors y with
+        // residuals r = |Hy - E y| / |y|.  A sector counts as converged when
+        // each value has r <= tol |E| or r^2 / gap <= tol |E| (the
+        // Rayleigh-quotient error is at most r^2 / gap), gap = the distance
+        // from E to the nearest FP32 Ritz value of another level, less r.
+        constexpr int KO = BV<K>::cplx ? 2 : 0;
+        using TO = typename BV<KO>::T;
+        const int ne = n_eig, zcap = kcap * b;
+        std::vector<double2> Zh((size_t)n * ne * zcap, make_double2(0, 0));
+        std::vector<std::vector<double>> raw(n);
+        auto ritz = [&](int sct) {
+            Band T;
+            std::vector<int> pos;
+            const int it = std::max(1, its_last[sct]);
+            build_T(sct, it, T, pos);
+            raw[sct] = band_lowest(T, ne + b + 1);  // far enough to see copies of a degenerate level
+            std::vector<std::vector<cd>> zs;
+            for (int e = 0; e < ne && e < (int)raw[sct].size(); ++e) {
+                std::vector<cd> z = band_vector(T, raw[sct][e], zs);
+                for (int q = 0; q < it * b; ++q)
+                    if (pos[q] >= 0) Zh[((size_t)sct * ne + e) * zcap + q] = make_double2(z[pos[q]].real(), z[pos[q]].imag());
+                zs.push_back(std::move(z));
+            }
+        };
+        {
+            const int nth = std::max(1, std::min<int>(n, (int)std::thread::hardware_concurrency()));
+            std::vector<std::thread> pool;
+            for (int t = 1; t < nth; ++t)
+                pool.emplace_back([&, t]() {
+                    for (int sct = t; sct < n; sct += nth) ritz(sct);
+                });
+            for (int sct = 0; sct < n; sct += nth) ritz(sct);
+            for (auto& th : pool) th.join();
+        }
+        for (int sct = 0; sct < n; ++sct) its_last[sct] = std::max(1, its_last[sct]);
+        double2* Zd = (double2*)get(Zh.size() * sizeof(double2));
+        int* its_d = (int*)get((size_t)n * 4);
+        int* act_all = (int*)get((size_t)n * 4);
+        TO* Y = (TO*)get((size_t)ne * tot * sizeof(TO));
+        TO* HY = (TO*)get((size_t)ne * tot * sizeof(TO));
+        double2* part2 = (double2*)get((size_t)nt * ne * ne * sizeof(double2));
+        double2* Cq = (double2*)get((size_t)n * ne * ne * sizeof(double2));
+        double* Ed = (double*)get((size_t)n * ne * sizeof(double));
+        if (!Zd || !its_d || !act_all || !Y || !HY || !part2 || !Cq || !Ed)
+            return fail(ED_ERR_NOMEM, "block Lanczos refinement workspace");
+        const std::vector<int> ones(n, 1);
+        ED_CUDA(cudaMemcpyAsync(Zd, Zh.data(), Zh.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+        ED_CUDA(cudaMemcpyAsync(its_d, its_last.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        ED_CUDA(cudaMemcpyAsync(act_all, ones.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        bl_combine<K, KO><<<g, 256, 0, s>>>(Y, ne, V, bs, Zd, zcap, its_d, ro, n, b);
+        ED_CUDA(cudaGetLastError());
+        BatchLaunch L2 = make_launch(B, KO == 0 ? ED_F64 : ED_C128, Y, HY, ne);
+        L2.active = act_all;
+        {
+            const ed_status st = apply_batch_launch(L2, s);
+            if (st != ED_OK) return st;
+        }
+        // per sector and column pair: sum_i conj(X_a[i]) Z_c[i]
+        auto sums = [&](const TO* X, const TO* Z, std::vector<double2>& out) -> ed_status {
+            bl_gram<KO><<<dim3(nt, 1), 256, 0, s>>>(X, 0, nullptr, Z, tiles, ro, ne, part2, nt, 0, act_all);
+            bl_reduce<<<n, 128, 0, s>>>(part2, tile_first, n, ne, nt, nullptr, 1, Cq, 0);
+            ED_CUDA(cudaGetLastError());
+            out.resize((size_t)n * ne * ne);
+            ED_CUDA(cudaMemcpyAsync(out.data(), Cq, out.size() * sizeof(double2), cudaMemcpyDeviceToHost, s));
+            ED_CUDA(cudaStreamSynchronize(s));
+            return ED_OK;
+        };
+        std::vector<double2> yhy, yy, rr;
+        ed_status st = sums(Y, HY, yhy);
+        if (st == ED_OK) st = sums(Y, Y, yy);
+        if (st != ED_OK) return st;
+        // Rayleigh-Ritz per sector on the span of its refined vectors
+        std::vector<double> E((size_t)n * ne, 0.0);
+        std::vector<double2> Ch((size_t)n * ne * ne, make_double2(0, 0));
+        std::vector<char> rr_ok(n, 1);
+        for (int sct = 0; sct < n; ++sct) {
+            std::vector<cd> Mh((size_t)ne * ne), Gh((size_t)ne * ne), Cs;
+            for (size_t q = 0; q < (size_t)ne * ne; ++q) {
+                const double2 m = yhy[(size_t)sct * ne * ne + q], gq = yy[(size_t)sct * ne * ne + q];
+                Mh[q] = cd(m.x, m.y);
+                Gh[q] = cd(gq.x, gq.y);
+            }
+            std::vector<double> Es;
+            if (small_ritz(ne, Mh, Gh, Es, Cs)) {
+                for (int e = 0; e < ne; ++e) E[(size_t)sct * ne + e] = Es[e];
+                for (size_t q = 0; q < (size_t)ne * ne; ++q)
+                    Ch[(size_t)sct * ne * ne + q] = make_double2(Cs[q].real(), Cs[q].imag());
+            } else {  // a degenerate subspace: keep the vectors, report unrefined values
+                rr_ok[sct] = 0;
+                for (int e = 0; e < ne; ++e) {
+                    E[(size_t)sct * ne + e] = cur[sct][e];
+                    Ch[((size_t)sct * ne + e) * ne + e] = make_double2(1, 0);
+                }
+            }
+        }
+        double2* Cd = (double2*)get(Ch.size() * sizeof(double2));
+        if (!Cd) return fail(ED_ERR_NOMEM, "block Lanczos refinement workspace");
+        ED_CUDA(cudaMemcpyAsync(Cd, Ch.data(), Ch.size() * sizeof(double2), cudaMemcpyHostToDevice, s));
+        bl_rotate<KO><<<g, 256, 0, s>>>(Y, HY, Cd, ne, ro, n);
+        ED_CUDA(cudaMemcpyAsync(Ed, E.data(), E.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+        bl_resid<KO><<<g, 256, 0, s>>>(HY, Y, Ed, ne, ro, n);
+        ED_CUDA(cudaGetLastError());
+        st = sums(HY, HY, rr);
+        if (st == ED_OK) st = sums(Y, Y, yy);
+        if (st != ED_OK) return st;
+        auto dg = [&](const std::vector<double2>& v, int sct, int e) { return v[((size_t)sct * ne + e) * ne + e].x; };
+        int certified = 0;
+        std::vector<int> polish(n, 0);
+        for (int sct = 0; sct < n; ++sct) {
+            if (only && !(*only)[sct]) continue;
+            bool ok = rr_ok[sct] != 0;
+            for (int e = 0; e < ne; ++e) {
+                const double en = E[(size_t)sct * ne + e], nrm = dg(yy, sct, e);
+                const double r = nrm > 0 ? std::sqrt(std::max(dg(rr, sct, e) / nrm, 0.0)) : 1e300;
+                const double sc = std::max(1.0, fabs(en));
+                // gap: distance to the nearest other level of T (values within
+                // max(10 r, 1e-6 |E|) of E count as copies of E's own level)
+                const double same = std::max(10.0 * r, 1e-6 * sc);
+                double gap = 1e300;
+                for (double q : raw[sct])
+                    if (fabs(q - en) > same) gap = std::min(gap, fabs(q - en));
+                gap = std::max(gap - r, 1e-300);
+                if (!(r <= o->tol * sc || r * r <= o->tol * sc * gap)) ok = false;
+                cur[sct][e] = en;
+            }
+            if (ok) ++certified;
+            else polish[sct] = 1;
+        }
+        // Sectors whose values the FP32 Ritz vectors cannot certify (a close
+        // next level) continue in FP64: block Lanczos with their refined
+        // vectors as the start block (one vector per value), only these
+        // sectors iterating; from such a start it converges in a few steps.
+        if (std::count(polish.begin(), polish.end(), 1) > 0) {
+            ed_block_lanczos_opts o2 = *o;
+            o2.dtype = KO == 0 ? ED_F64 : ED_C128;
+            o2.block = ne;
+            o2.reorth = 1;
+            o2.max_iter = std::min(o->max_iter, 60);
+            std::vector<double> ev2((size_t)n * ne, 0.0);
+            std::vector<char> ok2;
+            const ed_status st2 = block_lanczos<KO>(B, &o2, ev2.data(), nullptr, user_stream, Y, &polish, &ok2);
+            if (st2 != ED_OK && st2 != ED_ERR_NOT_CONVERGED) return st2;
+            for (int sct = 0; sct < n; ++sct)
+                if (polish[sct] && ok2[sct]) {
+                    for (int e = 0; e < ne; ++e) cur[sct][e] = ev2[(size_t)sct * ne + e];
+                    ++certified;
+                    polish[sct] = 0;
+                }
+        }
+        conv_all = certified;
+        for (int sct = 0; sct < n; ++sct) okv[sct] = (!only || (*only)[sct]) && !polish[sct];
     }
     for (int sct = 0; sct < n; ++sct)
         for (int e = 0; e < n_eig; ++e) evals[(size_t)sct * n_eig + e] = cur[sct][e];
@@ -853,7 +1321,8 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         rep->step_seconds = t_steps;
         rep->used_graph = gexec ? 1 : 0;
     }
-    return conv_all == n ? ED_OK : fail(ED_ERR_NOT_CONVERGED, "%d of %d sectors converged", conv_all, n);
+    if (conv) *conv = okv;
+    return conv_all == n_run ? ED_OK : fail(ED_ERR_NOT_CONVERGED, "%d of %d sectors converged", conv_all, n_run);
 }
 
 }  // namespace ed
@@ -867,10 +1336,19 @@ extern "C" ed_status ed_lanczos_batch(const ed_batch* B, const ed_block_lanczos_
     // blocks of several vectors keep full reorthogonalisation: without it, the
     // copies of converged values cannot be told from genuine multiplicities
     if (!o->reorth && o->block != 1) return fail(ED_ERR_ARG, "the plain recursion needs block = 1");
-    if (o->dtype == ED_F64) {
-        if (!B->all_real) return fail(ED_ERR_ARG, "a complex sector needs ED_C128");
-        return block_lanczos<0>(B, o, evals, rep, (cudaStream_t)stream);
+    if (o->dtype == ED_F64 || o->dtype == ED_F32) {
+        if (!B->all_real) return fail(ED_ERR_ARG, "a complex sector needs a complex dtype");
     }
-    if (o->dtype == ED_C128) return block_lanczos<2>(B, o, evals, rep, (cudaStream_t)stream);
-    return fail(ED_ERR_ARG, "block Lanczos supports ED_F64 and ED_C128");
+    if (o->dtype == ED_F32 || o->dtype == ED_C64) {
+        // FP32 vectors: the Ritz vectors for the FP64 refinement come from the stored blocks
+        if (!o->reorth) return fail(ED_ERR_ARG, "FP32 vectors need full reorthogonalisation");
+        if (o->n_eig > 8) return fail(ED_ERR_ARG, "FP32 vectors: n_eig at most 8");
+    }
+    switch (o->dtype) {
+        case ED_F64: return block_lanczos<0>(B, o, evals, rep, (cudaStream_t)stream);
+        case ED_F32: return block_lanczos<1>(B, o, evals, rep, (cudaStream_t)stream);
+        case ED_C128: return block_lanczos<2>(B, o, evals, rep, (cudaStream_t)stream);
+        case ED_C64: return block_lanczos<3>(B, o, evals, rep, (cudaStream_t)stream);
+    }
+    return fail(ED_ERR_ARG, "bad dtype");
 }

@@ -753,7 +753,12 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     z.nb = (int)std::max<int64_t>(1, std::min<int64_t>(1024, (D + 4095) / 4096));
     const int max_it = (int)std::min<int64_t>(o->max_iter, D);
     const int n_eig = std::min<int>(o->n_eig, (int)D);
-    const int nstore = o->reorth ? max_it + 1 : 3;
+    // plain recursion whose Ritz vectors are needed: keep its vectors on the
+    // device (host_vectors = 2) or in host memory (1), else a second pass
+    const bool need_vectors = !o->reorth && (evecs || ((K == 1 || K == 3) && o->refine > 0));
+    const bool keep_dev = need_vectors && o->host_vectors == 2;
+    const bool all_slots = o->reorth || keep_dev;
+    const int nstore = all_slots ? max_it + 1 : 3;
     T* V = (T*)z.get((size_t)nstore * D * sizeof(T));
     T* w = (T*)z.get((size_t)D * sizeof(T));
     // partials: (max_it + 2) vectors' worth for the Gram-Schmidt dots, and two
@@ -764,7 +769,7 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     double* beta_d = (double*)z.get(2 * sizeof(double));
     if (!V || !w || !partial || !coef || !beta_d) return fail(ED_ERR_NOMEM, "Lanczos workspace");
     const unsigned g = z.grid();
-    auto vec = [&](int k) -> T* { return V + (int64_t)(o->reorth ? k : (k % 3)) * D; };
+    auto vec = [&](int k) -> T* { return V + (int64_t)(all_slots ? k : (k % 3)) * D; };
     auto dot = [&](const T* A, int nk, const T* bv, double2* out) {
         multi_dot<K><<<dim3(z.nb, nk), 256, 0, s>>>(A, D, bv, D, partial);
         reduce_partials<<<std::min(nk, 1024), 256, 0, s>>>(partial, z.nb, nk, out);
@@ -780,9 +785,8 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
     // Lanczos vectors in host memory (plain recursion whose Ritz vectors are needed)
     HostKrylov hk;
     {
-        const bool need_vectors = !o->reorth && (evecs || ((K == 1 || K == 3) && o->refine > 0));
         int pageable = 0;
-        if (o->host_vectors && need_vectors)
+        if (o->host_vectors == 1 && need_vectors)
             ED_CUDA(cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, h->basis->device));
         if (pageable) {
             hk.vec_bytes = (((size_t)D * sizeof(T)) + 4095) & ~(size_t)4095;
@@ -985,7 +989,7 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
         Vsrc = (const T*)hk.base;
         Vld = (int64_t)(hk.vec_bytes / sizeof(T));
     }
-    const bool stored_vectors = o->reorth || hk.base;
+    const bool stored_vectors = all_slots || hk.base;
     if (!stored_vectors && nk > 0 && (evecs || want_refine)) {
         const int nacc = evecs ? nk : 0;
         const int ncol = nacc + ny;
@@ -1044,7 +1048,7 @@ static ed_status run(const ed_hamiltonian* h, const ed_lanczos_opts* o, double* 
             combine<K, T><<<g, 256, 0, s>>>((T*)evecs + (int64_t)k * D, Vsrc, Vld, iters, sd, D);
             ED_CUDA(cudaStreamSynchronize(s));
         }
-        if (hk.base) {  // without reorthogonalisation the Lanczos vectors are not orthogonal: normalise
+        if (!o->reorth) {  // without reorthogonalisation the Lanczos vectors are not orthogonal: normalise
             for (int k = 0; k < nk; ++k) {
                 T* ek = (T*)evecs + (int64_t)k * D;
                 dot(ek, 1, ek, coef);

@@ -153,3 +153,54 @@ def test_batched_stored_lanczos(P, tri12, block, reorth):
     for s, p in enumerate(tri12):
         ref = np.linalg.eigvalsh(oracle.csr(p).toarray())[:n_eig]
         assert np.allclose(ev[s, :len(ref)], ref, rtol=0, atol=1e-10 * max(1.0, abs(ref[0]))), (s, ev[s], ref)
+
+
+@pytest.mark.parametrize("block,stored", [(1, False), (4, False), (8, True), (1, True)])
+def test_batched_fp32_block_lanczos(P, tri12, block, stored):
+    """FP32 vectors (complex FP32: the batch has complex sectors), block Gram-Schmidt in FP32
+    arithmetic, then the FP64 refinement (Ritz vectors, one batched FP64 H.x,
+    Rayleigh-Ritz): every sector's lowest levels within 1e-10 of the oracle's dense
+    spectrum, with multiplicities up to the block size."""
+    bases = [P.Basis(p.sector) for p in tri12]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12)]
+    if stored:
+        for h in hs:
+            h.store()
+    batch = P.Batch(hs)
+    assert not batch.is_real
+    n_eig = 1 if block == 1 else 3
+    ev, rep = batch.lanczos(block=block, n_eig=n_eig, tol=1e-10, max_iter=300 if block == 1 else 40, seed=5,
+                            use_graph=True, reorth=True, dtype=P.ED_C64)
+    assert rep.converged_sectors == len(tri12)
+    for s, p in enumerate(tri12):
+        ref = np.linalg.eigvalsh(oracle.csr(p).toarray())[:n_eig]
+        assert np.allclose(ev[s, :len(ref)], ref, rtol=0, atol=1e-10 * max(1.0, abs(ref[0]))), (s, ev[s], ref)
+
+
+def test_batched_fp32_real_sectors(P):
+    """Real sectors only (the Gamma sectors of the 4x4 square with C4v): FP32 real vectors
+    and the real FP64 refinement, against the oracle."""
+    probs = [C.square([[4, 0], [0, 4]], 1.0, 0.3, irrep=irr) for irr in ("A1", "A2", "B1", "B2")]
+    bases = [P.Basis(p.sector) for p in probs]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, probs)]
+    batch = P.Batch(hs)
+    assert batch.is_real
+    ev, rep = batch.lanczos(block=2, n_eig=2, tol=1e-10, max_iter=60, seed=3, use_graph=True, reorth=True,
+                            dtype=P.ED_F32)
+    assert rep.converged_sectors == len(probs)
+    for s, p in enumerate(probs):
+        ref = np.linalg.eigvalsh(oracle.csr(p).toarray())[:2]
+        assert np.allclose(ev[s, :len(ref)], ref, rtol=0, atol=1e-10 * max(1.0, abs(ref[0]))), (s, ev[s], ref)
+
+
+def test_batched_fp32_needs_reorth(P, tri12):
+    """FP32 vectors need the stored blocks (full reorthogonalisation) and n_eig <= 8."""
+    bases = [P.Basis(p.sector) for p in tri12[:2]]
+    hs = [P.Hamiltonian(b, p.terms) for b, p in zip(bases, tri12[:2])]
+    batch = P.Batch(hs)
+    with pytest.raises(P.EdError) as e:
+        batch.lanczos(block=1, n_eig=1, tol=1e-10, max_iter=40, reorth=False, dtype=P.ED_C64)
+    assert e.value.name == "ED_ERR_ARG"
+    with pytest.raises(P.EdError) as e:
+        batch.lanczos(block=2, n_eig=9, tol=1e-10, max_iter=40, reorth=True, dtype=P.ED_C64)
+    assert e.value.name == "ED_ERR_ARG"

@@ -1,7 +1,8 @@
-"""Lanczos vectors of the plain recursion kept in host memory (host_vectors):
-the Ritz vectors and the mixed-precision refinement come from the stored
-vectors instead of a second pass, with the same results (the second pass
-regenerates the same vectors bit for bit)."""
+"""Lanczos vectors of the plain recursion kept in host memory (host_vectors = 1)
+or in device memory (host_vectors = 2): the Ritz vectors and the
+mixed-precision refinement come from the stored vectors instead of a second
+pass, with the same results (the second pass regenerates the same vectors bit
+for bit)."""
 import numpy as np
 import pytest
 
@@ -37,7 +38,7 @@ def test_host_vectors_match_second_pass(P, make):
     d64, d32 = (P.ED_F64, P.ED_F32) if real else (P.ED_C128, P.ED_C64)
     t64 = torch.float64 if real else torch.complex128
     out = {}
-    for hv in (False, True):
+    for hv in (0, 1, 2):
         # mixed precision, plain recursion: refined energy
         ev, rep = h.lanczos(n_eig=1, tol=1e-10, max_iter=300, dtype=d32, reorth=False, refine=True, host_vectors=hv)
         assert abs(ev[0] - ref[0]) <= 1e-10 * abs(ref[0]), (hv, ev[0], ref[0])
@@ -52,8 +53,11 @@ def test_host_vectors_match_second_pass(P, make):
             v = out[("evec", hv)][0][k].astype(np.complex128)
             r = H @ v - ev[k] * v
             assert np.linalg.norm(r) <= 1e-6 * abs(ev[k]) * np.linalg.norm(v)
-    assert out[("mixed", True)][0] == pytest.approx(out[("mixed", False)][0], rel=1e-13, abs=0)
-    # no second pass: one H.x per step instead of two
-    assert out[("evec", True)][1] == out[("evec", True)][2]
-    assert out[("evec", False)][1] > out[("evec", False)][2]
-    assert np.allclose(out[("evec", True)][0], out[("evec", False)][0], rtol=0, atol=1e-9)
+    for kept in (1, 2):
+        assert out[("mixed", kept)][0] == pytest.approx(out[("mixed", 0)][0], rel=1e-13, abs=0)
+        # no second pass: one H.x per step instead of two
+        assert out[("evec", kept)][1] == out[("evec", kept)][2]
+        assert np.allclose(out[("evec", kept)][0], out[("evec", 0)][0], rtol=0, atol=1e-9)
+    assert out[("evec", 0)][1] > out[("evec", 0)][2]
+    # the same vectors, whether kept on the host or on the device
+    assert np.array_equal(out[("evec", 1)][0], out[("evec", 2)][0])

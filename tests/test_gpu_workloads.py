@@ -172,3 +172,26 @@ def test_triangular24_batch_bench_config(P):
         dt = P.ED_F64 if h.is_real else P.ED_C128
         es, _ = h.lanczos(n_eig=1, tol=1e-12, max_iter=300, dtype=dt)
         assert abs(es[0] - ref) <= 1e-10 * abs(ref), (s, es[0], ref)
+
+
+@pytest.mark.parametrize("block", [1, 8])
+def test_triangular24_batch_fp32(P, block):
+    """The batching workload with FP32 vectors, as bench.py runs it (every sector's
+    structure stored, full reorthogonalisation, FP32 block Gram-Schmidt, FP64
+    refinement and, where needed, FP64 polish): every sector's ground energy within
+    1e-10 relative of the oracle's (tests/golden/eigenvalues.json)."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "eigenvalues.json")))
+    probs = C.triangular24_sectors()
+    bases = [P.Basis(q.sector) for q in probs]
+    hs = [P.Hamiltonian(bb, q.terms) for bb, q in zip(bases, probs)]
+    for h in hs:
+        h.store()
+    batch = P.Batch(hs)
+    ev, rep = batch.lanczos(block=block, n_eig=1, tol=1e-10, max_iter=300 if block == 1 else 80, seed=3,
+                            use_graph=True, reorth=True, dtype=P.ED_C64)
+    assert rep.converged_sectors == len(probs)
+    for s in range(len(probs)):
+        ref = gold[f"triangular24 {probs[s].meta['sector']}"]["eigenvalues"][0]
+        assert abs(ev[s, 0] - ref) <= 1e-10 * abs(ref), (s, ev[s, 0], ref)
