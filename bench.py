@@ -246,6 +246,15 @@ def matrix_free_bytes(D, G, s_x, s_st):
     return D * (s_st + 2 + 2 * s_x) + G * s_x
 
 
+def workload_config(problem, desc, dim):
+    """The `config` object both arms print: the workload's identity (cluster,
+    couplings, sector, its dimension) and the timing rule."""
+    return {"workload": desc, "dim": int(dim),
+            "n_terms": len(problem.terms.bonds) + len(problem.terms.tris), "n_sym": int(problem.sector.n_sym),
+            "n_sublat": int(problem.sector.n_sublat),
+            "l2": "GPU arm: L2 flushed (256 MB write) between timed steps; the inputs exceed L2 as well"}
+
+
 def lanczos_pair(pkg, torch, H, real, D, stream, store_for, hx_fp64_s=None):
     """Time-to-E0 (1e-10) of the FP64 run and of the mixed run (FP32 vectors, FP64
     refinement), each on H's stored structure as store_for(dtype) prepares it
@@ -505,7 +514,8 @@ def main():
         line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
                 "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": desc, "rows_per_step_sample": tot_rows // max(1, args.steps)},
+                "config": workload_config(problem, desc, oracle.sector_dim_formula(problem.sector)),
+                "run": {"rows_per_step_sample": tot_rows // max(1, args.steps), "host": "CPU oracle"},
                 "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
                                  "sample": f"oracle matrix-free rows on ~{budget:.2f} s random representative samples per step"},
                 "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -619,14 +629,12 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": sum(ms) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
-            "config": {"workload": desc, "dim": D, "n_terms": n_terms, "n_sym": int(problem.sector.n_sym),
-                       "n_sublat": int(problem.sector.n_sublat),
-                       "l2": "flushed: 256 MB write between timed steps (inputs also exceed L2)",
-                       "hx_path": "matrix-free" if args.matrix_free else
-                       "stored structure (built once per Hamiltonian with the schedule in `store`, outside the "
-                       "timed region)",
-                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
-                       "basis_build_s": round(t_basis, 3)},
+            "config": workload_config(problem, desc, D),
+            "run": {"hx_path": "matrix-free" if args.matrix_free else
+                    "stored structure (built once per Hamiltonian with the schedule in `store`, outside the "
+                    "timed region)",
+                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+                    "basis_build_s": round(t_basis, 3)},
             "roofline": {"bound": "hbm", "kernel": kernel, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic, "ncu_context": ncu_ctx,
                          "peak_source": f"{peak_kind} hbm_gbs", "algorithmic_bytes_per_launch": b_alg,
