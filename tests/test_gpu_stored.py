@@ -376,7 +376,7 @@ def _row_bound(problem, eps):
     return 64 * eps * R
 
 
-def _full_size(P, problem, dtypes, n_sample, seed, bitexact):
+def _full_size(P, problem, dtypes, n_sample, seed, bitexact, lanes=1):
     import torch
     b = P.Basis(problem.sector)
     reps, _ = b.export()
@@ -392,6 +392,8 @@ def _full_size(P, problem, dtypes, n_sample, seed, bitexact):
         h.apply(x, y_free)
         g_free, _ = h.counters()
         h.store(edt)
+        if lanes > 1:
+            h.store_set_lanes(lanes)
         info = h.store_info()
         assert info["entries"] == g_free
         y = torch.empty_like(x)
@@ -399,7 +401,7 @@ def _full_size(P, problem, dtypes, n_sample, seed, bitexact):
         torch.cuda.synchronize()
         single = tdt in (torch.float32, torch.complex64)
         eps = EPS32 if single else EPS64
-        if bitexact and info["segments"] == 1 and not cplx:
+        if bitexact and info["segments"] == 1 and not cplx and lanes == 1:
             assert torch.equal(y, y_free)
         else:
             d = (y - y_free).abs().max().item()
@@ -418,6 +420,14 @@ def test_stored_square32_bench_config(P):
     2.36e6 rows, and equal to the oracle's rows on sampled representatives."""
     import torch
     _full_size(P, C.square32(), [(torch.float64, P.ED_F64), (torch.float32, P.ED_F32)], 600, 3, True)
+
+
+def test_stored_square32_lanes(P):
+    """The 32-site workload with two lanes per row (the schedule the autotuner picks there):
+    FP64 and FP32 within the summation-order bound of the matrix-free kernel over all rows
+    and of the oracle's rows on sampled representatives."""
+    import torch
+    _full_size(P, C.square32(), [(torch.float64, P.ED_F64), (torch.float32, P.ED_F32)], 400, 5, True, lanes=2)
 
 
 def test_stored_kagome36(P):
