@@ -272,9 +272,9 @@ def lanczos_pair(pkg, torch, H, real, D, stream, store_for, hx_fp64_s=None):
                              ("mixed", pkg.ED_F32 if real else pkg.ED_C64, True)):
         store_s = store_for(dt)
         # the mixed run's plain-recursion vectors (up to 301 of them) stay on the
-        # device when they fit half the free memory, else they go to host memory
+        # device when they fit 70 % of the free memory, else they go to host memory
         free, _ = torch.cuda.mem_get_info()
-        keep = 0 if not refine else (2 if 301 * D * (4 if real else 8) <= 0.5 * free else 1)
+        keep = 0 if not refine else (2 if 301 * D * (4 if real else 8) <= 0.7 * free else 1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         ev, rep = H.lanczos(n_eig=1, tol=1e-10, max_iter=300, dtype=dt, reorth=False, refine=refine,
