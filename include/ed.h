@@ -506,6 +506,19 @@ ed_status ed_lanczos_tridiag(const ed_hamiltonian* h, ed_dtype dtype, const void
 ed_status ed_tridiag_eigs(const double* alpha, const double* beta, int32_t n, int32_t k, double eps_vectors,
                           int32_t filter, double* evals, int32_t* n_found);
 
+/* ed_band_eigs -- lowest k eigenpairs of a Hermitian band matrix T (the block
+ * tridiagonal T of block Lanczos has bandwidth 2 block - 1), the host solver
+ * ed_lanczos_batch uses.  band: HOST [n][bw+1][2], entry (i, q) = (Re, Im) of
+ * T[i][i-q] for q <= i (the lower band; the diagonal's imaginary part is
+ * ignored).  Eigenvalues by bisection on the inertia of T - x (banded LDL^H,
+ * FP64), ascending, into evals[k]; eigenvectors (evecs: HOST [k][n][2] or
+ * NULL) by inverse iteration with pivoting inside the band, each
+ * orthogonalised against the earlier ones (so degenerate values get
+ * orthonormal vectors).  *n_found = min(k, n).  Host only; no device is
+ * touched. */
+ed_status ed_band_eigs(const double* band, int32_t n, int32_t bw, int32_t k, double* evals, double* evecs,
+                       int32_t* n_found);
+
 /* ---------------------------------------------------------------- batches of sectors
  * A batch groups Hamiltonians of several sectors of one cluster (same number
  * of sites, state word and sublattice blocks, e.g. every momentum/irrep

@@ -4,4 +4,4 @@ The compute path is libed.so (hand-written CUDA, C ABI in include/ed.h);
 `ed` is its thin ctypes binding.
 """
 from .ed import (ED_C64, ED_C128, ED_F32, ED_F64, Basis, BasisSUN, Batch, EdError, Hamiltonian, lib,  # noqa: F401
-                 report_dict, representatives, sector_tables, tridiag_eigs)
+                 band_eigs, report_dict, representatives, sector_tables, tridiag_eigs)

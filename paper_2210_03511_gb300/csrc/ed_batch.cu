@@ -1327,6 +1327,36 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
 
 }  // namespace ed
 
+extern "C" ed_status ed_band_eigs(const double* band, int32_t n, int32_t bw, int32_t k, double* evals, double* evecs,
+                                  int32_t* n_found) {
+    if (!band || !evals || n < 1 || bw < 0 || k < 1) return fail(ED_ERR_ARG, "bad argument");
+    if (bw > n - 1) bw = n - 1;
+    Band T;
+    T.n = n;
+    T.bw = bw;
+    T.L.assign((size_t)n * (bw + 1), cd(0));
+    for (int i = 0; i < n; ++i)
+        for (int q = 0; q <= bw && q <= i; ++q) {
+            const double* v = band + 2 * ((size_t)i * (bw + 1) + q);
+            T.at(i, q) = q == 0 ? cd(v[0], 0.0) : cd(v[0], v[1]);  // the diagonal of a Hermitian T is real
+        }
+    const std::vector<double> lam = band_lowest(T, k);
+    std::vector<std::vector<cd>> zs;
+    for (size_t e = 0; e < lam.size(); ++e) {
+        evals[e] = lam[e];
+        if (evecs) {
+            std::vector<cd> z = band_vector(T, lam[e], zs);
+            for (int i = 0; i < n; ++i) {
+                evecs[2 * ((size_t)e * n + i)] = z[i].real();
+                evecs[2 * ((size_t)e * n + i) + 1] = z[i].imag();
+            }
+            zs.push_back(std::move(z));
+        }
+    }
+    if (n_found) *n_found = (int32_t)lam.size();
+    return ED_OK;
+}
+
 extern "C" ed_status ed_lanczos_batch(const ed_batch* B, const ed_block_lanczos_opts* o, double* evals,
                                       ed_block_lanczos_report* rep, ed_stream stream) {
     if (!B || !o || !evals) return fail(ED_ERR_ARG, "null argument");

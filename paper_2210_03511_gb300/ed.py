@@ -119,6 +119,7 @@ def lib():
         L.ed_apply_autotune.argtypes = [c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp, P(c_i32)]
         L.ed_apply_set_blocks.argtypes = [c_vp, ctypes.c_int, c_i32, c_i32]
         L.ed_tridiag_eigs.argtypes = [P(c_dbl), P(c_dbl), c_i32, c_i32, c_dbl, c_i32, P(c_dbl), P(c_i32)]
+        L.ed_band_eigs.argtypes = [P(c_dbl), c_i32, c_i32, c_i32, P(c_dbl), P(c_dbl), P(c_i32)]
         L.ed_expectation.argtypes = [c_vp, ctypes.c_int, c_vp, c_i32, c_vp, P(c_dbl)]
         L.ed_time_evolve.argtypes = [c_vp, ctypes.c_int, c_vp, c_dbl, c_i32, c_vp, P(c_dbl), P(c_i32)]
         L.ed_restrict.argtypes = [c_vp, c_vp, ctypes.c_int, c_vp, c_vp, c_i32, c_vp]
@@ -179,6 +180,22 @@ def tridiag_eigs(alpha, beta, k, eps_vectors=2.0 ** -53, filter=True):
     check(lib().ed_tridiag_eigs(_ptr(a, c_dbl), _ptr(b, c_dbl), len(a), k, eps_vectors, int(filter),
                                 _ptr(out, c_dbl), ctypes.byref(nf)))
     return out[:nf.value]
+
+
+def band_eigs(band, k, vectors=True):
+    """ed_band_eigs: lowest k eigenpairs of a Hermitian band matrix given by its lower
+    band (complex array [n][bw+1], entry (i, q) = T[i][i-q]); host only.  Returns
+    (eigenvalues, eigenvectors as rows or None)."""
+    L = np.asarray(band, dtype=np.complex128)
+    n, w = L.shape
+    buf = np.ascontiguousarray(np.stack([L.real, L.imag], axis=-1), dtype=np.float64)
+    ev = np.zeros(k, np.float64)
+    vec = np.zeros((k, n, 2), np.float64) if vectors else None
+    nf = c_i32()
+    check(lib().ed_band_eigs(_ptr(buf, c_dbl), n, w - 1, k, _ptr(ev, c_dbl),
+                             _ptr(vec, c_dbl) if vectors else None, ctypes.byref(nf)))
+    m = nf.value
+    return ev[:m], (vec[:m, :, 0] + 1j * vec[:m, :, 1]) if vectors else None
 
 
 def sector_tables(sector) -> dict:

@@ -205,3 +205,58 @@ def test_tridiag_ghost_filter(P, dt):
     # a short run without ghosts: filtering changes nothing
     a2, b2 = _plain_lanczos(A, 40, np.float64, 3)
     assert np.array_equal(P.tridiag_eigs(a2, b2[:-1], 3, filter=True), P.tridiag_eigs(a2, b2[:-1], 3, filter=False))
+
+
+def _lower_band(A, bw):
+    n = A.shape[0]
+    L = np.zeros((n, bw + 1), complex)
+    for i in range(n):
+        for q in range(min(bw, i) + 1):
+            L[i, q] = A[i, i - q]
+    return L
+
+
+@pytest.mark.parametrize("bw", [1, 3, 15])
+def test_band_eigs_against_lapack(P, bw):
+    """ed_band_eigs (the host solver of block Lanczos) on random complex Hermitian band
+    matrices: eigenvalues equal LAPACK's (numpy.linalg.eigvalsh) to 1e-12 of |T|, and each
+    eigenvector has a residual below 1e-10 |T| and is orthonormal to the others."""
+    rng = np.random.default_rng(bw)
+    n = 90
+    A = np.zeros((n, n), complex)
+    for i in range(n):
+        for j in range(max(0, i - bw), i):
+            A[i, j] = rng.normal() + 1j * rng.normal()
+        A[i, i] = rng.normal()
+    A = np.tril(A, -1) + np.tril(A, -1).conj().T + np.diag(np.diag(A).real)
+    ref = np.linalg.eigvalsh(A)
+    k = 6
+    ev, Z = P.band_eigs(_lower_band(A, bw), k)
+    scale = np.abs(A).sum(axis=1).max()
+    assert len(ev) == k and np.allclose(ev, ref[:k], rtol=0, atol=1e-12 * scale), (ev, ref[:k])
+    for e in range(k):
+        assert np.linalg.norm(A @ Z[e] - ev[e] * Z[e]) <= 1e-10 * scale
+    assert np.allclose(Z.conj() @ Z.T, np.eye(k), atol=1e-10)
+
+
+def test_band_eigs_degenerate_levels(P):
+    """Two identical uncoupled blocks: every eigenvalue is doubly degenerate (the copies a
+    block Lanczos run holds); the solver returns each value twice with orthonormal vectors
+    spanning the level."""
+    rng = np.random.default_rng(7)
+    m, bw = 30, 3
+    B = np.zeros((m, m))
+    for i in range(m):
+        for j in range(max(0, i - bw), i):
+            B[i, j] = B[j, i] = rng.normal()
+        B[i, i] = rng.normal()
+    A = np.zeros((2 * m, 2 * m), complex)
+    A[:m, :m] = B
+    A[m:, m:] = B
+    ref = np.linalg.eigvalsh(B)
+    ev, Z = P.band_eigs(_lower_band(A, bw), 4)
+    assert np.allclose(ev, [ref[0], ref[0], ref[1], ref[1]], rtol=0, atol=1e-12 * np.abs(B).sum(axis=1).max())
+    assert np.allclose(Z.conj() @ Z.T, np.eye(4), atol=1e-10)
+    for e in range(4):
+        assert np.linalg.norm(A @ Z[e] - ev[e] * Z[e]) <= 1e-9
+    assert len(P.band_eigs(_lower_band(A, bw), 200, vectors=False)[0]) == 2 * m   # at most n values
