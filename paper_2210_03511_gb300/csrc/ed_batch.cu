@@ -22,6 +22,7 @@
 #include <chrono>
 #include <complex>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "ed_internal.h"
@@ -198,11 +199,14 @@ __global__ void bl_reduce(const double2* partial, const int* tile_first, int n, 
 }
 
 // W[c][i] -= sum_{j <= jmax} sum_a X_j[a][i] C[s][j][a][c]
-template <int K>
+// B: the block size at compile time (1, 2, 4, 8; the per-row accumulators
+// then live in registers), or 0 for any b <= MAXB.
+template <int K, int B = 0>
 __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int64_t xs, const int* jmax,
-                          const double2* C, int jcap, const int64_t* row_off, int n, int b, int local,
+                          const double2* C, int jcap, const int64_t* row_off, int n, int b_run, int local,
                           const int* active, const float2* Cf = nullptr) {
     using A = typename BV<K>::A;
+    const int b = B ? B : b_run;
     const int64_t total = row_off[n];
     const int jm = *jmax;
     const int j0 = local ? max(0, jm - 1) : 0;
@@ -213,13 +217,19 @@ __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int6
         const int64_t i = r - row_off[s];
         const int64_t D = row_off[s + 1] - row_off[s];
         const int64_t base = (int64_t)b * row_off[s];
-        A w[MAXB];
-        for (int c = 0; c < b; ++c) w[c] = c_ld(W[base + (int64_t)c * D + i]);
+        A w[B ? B : MAXB];
+#pragma unroll
+        for (int c = 0; c < (B ? B : MAXB); ++c)
+            if (c < b) w[c] = c_ld(W[base + (int64_t)c * D + i]);
         for (int j = j0; j <= jm; ++j) {
             const int64_t cj = ((int64_t)s * jcap + j) * bb;
-            for (int a = 0; a < b; ++a) {
+#pragma unroll
+            for (int a = 0; a < (B ? B : MAXB); ++a) {
+                if (a >= b) break;
                 const A x = c_ld(X[(int64_t)j * xs + base + (int64_t)a * D + i]);
-                for (int c = 0; c < b; ++c) {
+#pragma unroll
+                for (int c = 0; c < (B ? B : MAXB); ++c) {
+                    if (c >= b) break;
                     A cv;
                     if constexpr (BV<K>::single) cv = Cf[cj + a * b + c];
                     else cv = C[cj + a * b + c];
@@ -229,7 +239,9 @@ __global__ void bl_update(typename BV<K>::T* W, const typename BV<K>::T* X, int6
                 }
             }
         }
-        for (int c = 0; c < b; ++c) c_st(W[base + (int64_t)c * D + i], w[c]);
+#pragma unroll
+        for (int c = 0; c < (B ? B : MAXB); ++c)
+            if (c < b) c_st(W[base + (int64_t)c * D + i], w[c]);
     }
 }
 
@@ -300,11 +312,12 @@ __global__ void bl_chol(const double2* G, int jcap, int n, int b, double2* Rinv,
 }
 
 // Out[c][i] = sum_a W[a][i] Rinv[s][a][c]; Out may be W + (*kout)*os (device index) or W itself
-template <int K>
+template <int K, int B = 0>
 __global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int64_t os, const int* kout, int kadd,
-                         const double2* Rinv, const int64_t* row_off, int n, int b, const int* active,
+                         const double2* Rinv, const int64_t* row_off, int n, int b_run, const int* active,
                          const float2* Rinvf = nullptr) {
     using A = typename BV<K>::A;
+    const int b = B ? B : b_run;
     const int64_t total = row_off[n];
     typename BV<K>::T* out = Out + (kout ? (int64_t)(*kout + kadd) * os : 0);
     const int bb = b * b;
@@ -314,11 +327,17 @@ __global__ void bl_scale(const typename BV<K>::T* W, typename BV<K>::T* Out, int
         const int64_t i = r - row_off[s];
         const int64_t D = row_off[s + 1] - row_off[s];
         const int64_t base = (int64_t)b * row_off[s];
-        A w[MAXB];
-        for (int a = 0; a < b; ++a) w[a] = c_ld(W[base + (int64_t)a * D + i]);
-        for (int c = 0; c < b; ++c) {
+        A w[B ? B : MAXB];
+#pragma unroll
+        for (int a = 0; a < (B ? B : MAXB); ++a)
+            if (a < b) w[a] = c_ld(W[base + (int64_t)a * D + i]);
+#pragma unroll
+        for (int c = 0; c < (B ? B : MAXB); ++c) {
+            if (c >= b) break;
             A v{0, 0};
-            for (int a = 0; a < b; ++a) {
+#pragma unroll
+            for (int a = 0; a < (B ? B : MAXB); ++a) {
+                if (a >= b) break;
                 A rv;
                 if constexpr (BV<K>::single) rv = Rinvf[(int64_t)s * bb + a * b + c];
                 else rv = Rinv[(int64_t)s * bb + a * b + c];
@@ -916,6 +935,16 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
     const int64_t* ro = (const int64_t*)B->d_row_off.p;
     const int64_t* tiles = (const int64_t*)B->d_tiles.p;
     const HxArgs* desc = (const HxArgs*)B->d_desc.p;
+    // the elementwise block kernels specialised for the block size
+    auto with_b = [&](auto f) {
+        switch (b) {
+            case 1: f(std::integral_constant<int, 1>{}); break;
+            case 2: f(std::integral_constant<int, 2>{}); break;
+            case 4: f(std::integral_constant<int, 4>{}); break;
+            case 8: f(std::integral_constant<int, 8>{}); break;
+            default: f(std::integral_constant<int, 0>{}); break;
+        }
+    };
     // start block V_0 = orth(X), via CholQR2 on the Gaussian block
     if (start) ED_CUDA(cudaMemcpyAsync(W, start, (size_t)bs * sizeof(T), cudaMemcpyDeviceToDevice, s));
     else bl_init<K><<<g, 256, 0, s>>>(W, desc, ro, n, b, o->seed, B->w8 ? 8 : 4);
@@ -924,8 +953,11 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
             bl_gram<K><<<dim3(nt, 1), 256, 0, s>>>(src, 0, nullptr, src, tiles, ro, b, part, nt, 0, active);
             bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, nullptr, kcap, G, 0);
             bl_chol<<<(n + 63) / 64, 64, 0, s>>>(G, kcap, n, b, Rinv, Bacc, pass == 0, active, Rinvf);
-            bl_scale<K><<<g, 256, 0, s>>>(src, pass == 0 ? src : dst, dst_os, pass == 0 ? nullptr : kout, kadd, Rinv,
-                                          ro, n, b, active, Rinvf);
+            with_b([&](auto bt) {
+                bl_scale<K, decltype(bt)::value><<<g, 256, 0, s>>>(src, pass == 0 ? src : dst, dst_os,
+                                                                   pass == 0 ? nullptr : kout, kadd, Rinv, ro, n, b,
+                                                                   active, Rinvf);
+            });
         }
     };
     bl_set_int<<<1, 1, 0, s>>>(dk, 0);
@@ -952,7 +984,9 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
             const int win = (local || pass == 1) ? 1 : 0;
             bl_gram<K><<<dim3(nt, win ? 2 : kcap), 256, 0, s>>>(V, bs, dk, W, tiles, ro, b, part, nt, win, active);
             bl_reduce<<<n, 128, 0, s>>>(part, tile_first, n, b, nt, dk, kcap, Cp, win, Cpf);
-            bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, win, active, Cpf);
+            with_b([&](auto bt) {
+                bl_update<K, decltype(bt)::value><<<g, 256, 0, s>>>(W, V, bs, dk, Cp, kcap, ro, n, b, win, active, Cpf);
+            });
         }
         cholqr(W, V, bs, dk, 1);  // V_{k+1} = W R^-1, B_k accumulated in Bacc
         bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
@@ -965,7 +999,9 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
         if (st != ED_OK) return st;
         ED_CUDA(cudaMemsetAsync(C1, 0, (size_t)n * kcap * bb * sizeof(double2), s));
         if (single) ED_CUDA(cudaMemsetAsync(C1f, 0, (size_t)n * kcap * bb * sizeof(float2), s));
-        bl_update<K><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b, local, active, C1f);
+        with_b([&](auto bt) {
+            bl_update<K, decltype(bt)::value><<<g, 256, 0, s>>>(W, V, bs, dk, C1, kcap, ro, n, b, local, active, C1f);
+        });
         bl_save<<<1, 256, 0, s>>>(C1, C2, Bacc, kcap, n, b, dk, Ahist, Bhist, kcap, active);
         bl_set_int<<<1, 1, 0, s>>>(dk, 0);
         ED_CUDA(cudaGetLastError());
