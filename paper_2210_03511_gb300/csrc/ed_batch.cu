@@ -1126,13 +1126,21 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
                 }
                 if ((int)lam.size() > n_eig) lam.resize(n_eig);
             } else {
-                // blocks: the Ritz vector z of each value (inverse iteration on
-                // T) gives the residual |H y - lam y| = |B_last z_last| of
-                // y = V z, z_last the components in the last block
-                lam = band_lowest(T, n_eig + b);
-                ok = (int)lam.size() >= n_eig;
+                // blocks: the wanted values first; only when all of them are
+                // steady, the Ritz vector z of each (inverse iteration on T)
+                // gives the residual |H y - lam y| = |B_last z_last| of y = V z
+                // (z_last: the components in the last block), and only when
+                // that alone does not settle it, b further values of T give
+                // the gap (the host's band solves cost more than a step)
+                lam = band_lowest(T, n_eig);
+                ok = (int)lam.size() == n_eig;
+                for (int e = 0; e < n_eig && ok; ++e) {
+                    const double sc = std::max(1.0, fabs(lam[e]));
+                    if (fabs(lam[e] - prev[sct][e]) > std::max(0.1 * o->tol * sc, floor32)) ok = false;
+                }
                 const double2* Bl = &Bh[((size_t)sct * kcap + iters - 1) * bb];
                 std::vector<std::vector<cd>> zs;
+                std::vector<double> more;  // n_eig + b lowest values, when a gap is needed
                 for (int e = 0; e < n_eig && ok; ++e) {
                     std::vector<cd> z = band_vector(T, lam[e], zs);
                     double rb = 0.0;
@@ -1147,13 +1155,18 @@ static ed_status block_lanczos(const ed_batch* B, const ed_block_lanczos_opts* o
                     rb = std::sqrt(rb);
                     zs.push_back(std::move(z));
                     const double sc = std::max(1.0, fabs(lam[e]));
+                    if (rb <= std::max(o->tol * sc, floor32)) continue;
+                    if (rb * rb > o->tol * sc * 2.0 * band_norm(T)) {  // no gap of T is that wide
+                        ok = false;
+                        continue;
+                    }
+                    if (more.empty()) more = band_lowest(T, n_eig + b);
                     const double same = std::max(10.0 * rb, 1e-6 * sc);  // copies of the same level
                     double gap = 1e300;
-                    for (double q : lam)
+                    for (double q : more)
                         if (fabs(q - lam[e]) > same) gap = std::min(gap, fabs(q - lam[e]));
-                    if (!(rb <= std::max(o->tol * sc, floor32) || rb * rb <= o->tol * sc * gap)) ok = false;
+                    if (!(rb * rb <= o->tol * sc * gap)) ok = false;
                 }
-                if ((int)lam.size() > n_eig) lam.resize(n_eig);
             }
             for (int e = 0; e < (int)lam.size(); ++e) {
                 cur[sct][e] = lam[e];
